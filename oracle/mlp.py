@@ -1,0 +1,96 @@
+"""FP64 oracle of the learned gain surrogate (no counterpart in the paper).
+
+TEST INFRASTRUCTURE ONLY.  A camera's 3x36x64 thumbnail (box means of its
+uncorrected RGB, /255 - 0.5) goes through Linear(6912, 256) - ReLU -
+Linear(256, 256) - ReLU - Linear(256, 3) and predicts the camera's three
+log-gains; the labels are the log-gains of the per-camera gain fit (one
+block).  The GPU stores operands in BF16 and accumulates in FP32; this
+oracle computes in float64 and, when ``bf16`` is set, rounds to BF16 at the
+same storage points (the input, the weights as used, the hidden activations
+and their gradients) so that the two differ only by accumulation order.
+Weight layout: W1 [256, 6912], W2 [256, 256], W3 [3, 256] (out x in).
+"""
+from __future__ import annotations
+
+from typing import Dict
+
+import numpy as np
+
+D_IN, D_H, D_OUT = 3 * 36 * 64, 256, 3
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest BF16 value (ties to even) via float32."""
+    f = np.ascontiguousarray(np.asarray(x, np.float64).astype(np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def thumb_features(sums: np.ndarray, W: int, H: int) -> np.ndarray:
+    """[3, 36, 64] cell sums -> 6912 features: cell mean / 255 - 0.5."""
+    th, tw = sums.shape[1], sums.shape[2]
+    cw = np.array([(i + 1) * W // tw - i * W // tw for i in range(tw)], np.float64)
+    chh = np.array([(j + 1) * H // th - j * H // th for j in range(th)], np.float64)
+    area = chh[:, None] * cw[None, :]
+    return (sums.astype(np.float64) / area[None] / 255.0 - 0.5).reshape(-1)
+
+
+def forward(P: Dict[str, np.ndarray], X: np.ndarray, bf16: bool = True):
+    r = bf16_round if bf16 else (lambda a: np.asarray(a, np.float64))
+    x = r(X)
+    z1 = x @ r(P["W1"]).T + P["b1"]
+    h1 = r(np.maximum(z1, 0.0))
+    z2 = h1 @ r(P["W2"]).T + P["b2"]
+    h2 = r(np.maximum(z2, 0.0))
+    y = h2 @ r(P["W3"]).T + P["b3"]
+    return y, {"x": x, "z1": z1, "h1": h1, "z2": z2, "h2": h2, "y": y}
+
+
+def mse(y: np.ndarray, t: np.ndarray) -> float:
+    return float(np.mean((y - t) ** 2))
+
+
+def backward(P: Dict[str, np.ndarray], cache, t: np.ndarray, bf16: bool = True):
+    """Gradients of mean((y - t)^2) over the batch and the three outputs."""
+    r = bf16_round if bf16 else (lambda a: np.asarray(a, np.float64))
+    N = t.shape[0]
+    dy = 2.0 * (cache["y"] - t) / (N * D_OUT)
+    g = {"W3": dy.T @ cache["h2"], "b3": dy.sum(0)}
+    dh2 = r((dy @ r(P["W3"])) * (cache["z2"] > 0))
+    g["W2"] = dh2.T @ cache["h1"]
+    g["b2"] = dh2.sum(0)
+    dh1 = r((dh2 @ r(P["W2"])) * (cache["z1"] > 0))
+    g["W1"] = dh1.T @ cache["x"]
+    g["b1"] = dh1.sum(0)
+    return g
+
+
+def adam_step(P, G, state, lr: float, t: int, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015) of the FP32 master weights, in FP64."""
+    for k in P:
+        m = state.setdefault("m_" + k, np.zeros_like(P[k]))
+        v = state.setdefault("v_" + k, np.zeros_like(P[k]))
+        m[...] = b1 * m + (1 - b1) * G[k]
+        v[...] = b2 * v + (1 - b2) * G[k] * G[k]
+        mh = m / (1 - b1 ** t)
+        vh = v / (1 - b2 ** t)
+        P[k] = P[k] - lr * mh / (np.sqrt(vh) + eps)
+    return P
+
+
+def regauge(logg: np.ndarray, groups) -> np.ndarray:
+    """Subtract each chain's mean log-gain (per channel): the common scale of
+    a chain is unobservable, so predictions are compared in the gauge of the
+    labels (sum of log-gains zero over the chain)."""
+    out = np.array(logg, np.float64, copy=True)
+    groups = np.asarray(groups)
+    for g in np.unique(groups):
+        m = groups == g
+        out[m] -= out[m].mean(0, keepdims=True)
+    return out
+
+
+def gain_error(pred_log: np.ndarray, label_log: np.ndarray) -> np.ndarray:
+    """max over channels of |exp(pred - label) - 1| per camera."""
+    return np.abs(np.exp(pred_log - label_log) - 1.0).max(-1)

@@ -1,0 +1,84 @@
+"""Frame-set level pins of the oracle against what the paper reports.
+
+The paper's seam-cost table (Table "Average values of the cost function")
+was measured on proprietary video that is not available, so its numbers
+cannot be reproduced; what it fixes qualitatively is pinned instead on
+synthetic arrays: the corrected seam cost is far below the uncorrected one
+and stays above the interior value.  Also pinned: the paper's constants
+(golden fixture) are the oracle's defaults, the lagged schedule corrects
+its first frame set with the identity, and the per-camera gains of the full
+NV12 path recover the synthetic camera gains.
+"""
+import os
+
+import numpy as np
+
+from paper_1910_03517_gb300 import synth
+from conftest import np_frames
+from oracle import seamcost
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+
+
+def _golden():
+    out = {}
+    for line in open(GOLDEN):
+        if line.strip() and not line.startswith("#"):
+            name, val = line.split()[:2]
+            out[name] = float(val)
+    return out
+
+
+def test_defaults_are_the_papers_constants(orc):
+    g = _golden()
+    assert orc.Params().alpha == g["alpha"]
+    # the table's ordering: interior < corrected < uncorrected, both scenes
+    for w in ("sunny", "cloudy"):
+        assert g[f"seam_cost_{w}_interior"] < g[f"seam_cost_{w}_corrected"] < g[f"seam_cost_{w}_uncorrected"]
+
+
+def _run(orc, wl, params, frames):
+    o = orc.ArrayOracle(wl.cams, params)
+    out = None
+    for t in range(frames):
+        out = o.step(np_frames(synth.frame_set(wl, t)), want_frame_stats=False)
+    return out
+
+
+def test_correction_lowers_seam_cost(orc):
+    wl = synth.tower12(frames=3)
+    wl.cams = [synth.Camera(1024, 540, position=i) for i in range(4)]
+    wl.glare_cams = ()
+    for mode, B in ((orc.FIT_GLOBAL, 1), (orc.FIT_SEAM_AFFINE, 16)):
+        r = _run(orc, wl, orc.Params(fit_mode=mode, num_blocks=B), 2)
+        unc = np.mean([seamcost.seam_cost(r["rgb"][k], r["rgb"][k + 1]) for k in range(3)])
+        cor = np.mean([seamcost.seam_cost(r["corrected"][k], r["corrected"][k + 1]) for k in range(3)])
+        inner = np.mean([seamcost.interior_cost(r["rgb"][k]) for k in range(4)])
+        assert cor < 0.5 * unc, (mode, unc, cor)
+        assert inner < cor
+
+
+def test_lagged_first_frame_is_identity(orc):
+    wl = synth.small_pair()
+    o = orc.ArrayOracle(wl.cams, orc.Params(schedule=orc.SCHED_LAGGED))
+    r0 = o.step(np_frames(synth.frame_set(wl, 0)))
+    for k in range(2):
+        assert (r0["corrected"][k] == r0["rgb"][k]).all()
+    r1 = o.step(np_frames(synth.frame_set(wl, 1)))
+    assert np.array_equal(r1["maps"], r0["E"])
+
+
+def test_nv12_path_recovers_camera_gains(orc):
+    import torch
+    cams = [synth.Camera(640, 480, position=i) for i in range(3)]
+    wl = synth.Workload("mirror", cams, frames=1, seed=4, mirror_seams=True, noise_sigma=2.0)
+    d = torch.tensor([[0.7, 0.9, 0.8], [0.95, 0.65, 0.75], [0.8, 0.8, 0.6]], dtype=torch.float64)
+    frames = []
+    for k, cam in enumerate(cams):
+        y, uv = synth.encode_nv12(synth.camera_rgb8(wl, k, 0, gains=d), cam.y_pitch, cam.uv_pitch)
+        frames.append({"y": y.numpy(), "uv": uv.numpy()})
+    r = orc.ArrayOracle(cams, orc.Params()).step(frames)
+    g = r["maps"][:, 0, 0, :, 0]
+    want = 1.0 / d.numpy()
+    want /= np.exp(np.log(want).mean(0))
+    assert np.abs(g / want - 1).max() < 0.02
