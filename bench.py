@@ -1,0 +1,441 @@
+#!/usr/bin/env python
+"""Throughput of the camera-array exposure / white-balance hot path on GB300.
+
+A step is one frame set of the array through the whole path: band statistics
+with object removal (pass A), the FP64 fit with smoothing and quantisation
+(solve), and conversion + whole-frame histograms + Q16 application (pass B),
+plus the crops when the workload has them.  Default workload: 12 cameras of
+2048x1080 NV12 (26.5 MP per frame set), per-camera gains, current schedule.
+
+Inputs are a ring of distinct synthetic frame sets resident in HBM (larger
+than 4x L2, so every step reads from DRAM); the library processes the ring
+through a captured CUDA graph.  `value` = corrected input megapixels per
+second over all ranks; `e2e` = the same through the host-buffer entry point
+with host->device input copies and device->host output copies in the timed
+region.  `--impl reference` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALG_BYTES_NV12 = 4.5      # read 1.5 B/px (Y + UV/2), write 3 B/px RGB24
+ALG_BYTES_MONO = 5.0      # read 2 B/px, write 3 B/px
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=24000)
+    ap.add_argument("--warmup", type=int, default=48)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tower12", choices=["tower12", "small", "uneven", "stress"])
+    ap.add_argument("--fit", default="global", choices=["global", "affine"])
+    ap.add_argument("--schedule", default="current", choices=["current", "lagged"])
+    ap.add_argument("--ring", type=int, default=0, help="distinct input frame sets (multiple of 6)")
+    ap.add_argument("--e2e-steps", type=int, default=120)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1910_03517_gb300 import synth
+    return {"tower12": synth.tower12, "small": synth.small_pair, "uneven": synth.uneven_array,
+            "stress": synth.stress24}[name]()
+
+
+def alg_bytes(wl):
+    from paper_1910_03517_gb300 import synth
+    b = 0.0
+    for c in wl.cams:
+        b += (ALG_BYTES_MONO if c.fmt == synth.MONO16 else ALG_BYTES_NV12) * c.width * c.height
+    return b
+
+
+def input_bytes(wl):
+    from paper_1910_03517_gb300 import synth
+    tot = 0
+    for c in wl.cams:
+        tot += c.y_pitch * c.height + (c.uv_pitch * (c.height // 2) if c.fmt == synth.NV12 else 0)
+    return tot
+
+
+def array_kwargs(args, wl):
+    from paper_1910_03517_gb300 import rt
+    kw = dict(flags=rt.RT_FLAG_FRAME_STATS,
+              fit_mode=rt.RT_FIT_GLOBAL if args.fit == "global" else rt.RT_FIT_SEAM_AFFINE,
+              num_blocks=1 if args.fit == "global" else 16,
+              schedule=rt.RT_SCHED_CURRENT if args.schedule == "current" else rt.RT_SCHED_LAGGED)
+    if wl.n_crops:
+        kw.update(max_crops=wl.n_crops, crop_size=wl.crop_out)
+    return kw
+
+
+def config_dict(args, wl, ring_desc):
+    return {"workload": wl.name, "cameras": len(wl.cams), "pixels_per_set": wl.pixels,
+            "fit": ("per-camera gains, 1 block" if args.fit == "global" else "seam affine maps, 16 blocks"),
+            "schedule": args.schedule, "crops_per_set": wl.n_crops, "l2": ring_desc}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 8 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) > 8:
+                for i, n in enumerate(names):
+                    if "Active" in r[5 + i] and "Not" not in r[5 + i]:
+                        reasons.add(n)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline inputs
+# ---------------------------------------------------------------------------
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def pass_b_source_sha():
+    h = hashlib.sha256()
+    for f in ("k_pass_b.cu", "pixel.cuh", "rt_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1910_03517_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload_name):
+    """DRAM bytes per pass-B launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "pass_b_%s.md" % workload_name)
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"source_sha256_16\s*=\s*([0-9a-f]+)", txt)
+    m_tr = re.search(r"traffic_bytes_per_launch\s*=\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_tr or m_sha.group(1) != pass_b_source_sha():
+        return None
+    return float(m_tr.group(1))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def cpu_rows_sample(wl, rows):
+    """The same array with every camera cut to its first `rows` rows."""
+    import copy
+    from paper_1910_03517_gb300 import synth
+    w2 = copy.deepcopy(wl)
+    for c in w2.cams:
+        c.height = max(2, min(c.height, rows - rows % 2))
+    return w2
+
+
+def oracle_frames_host(wl, t):
+    from paper_1910_03517_gb300 import synth
+    return [{k: v.cpu().numpy() for k, v in f.items()} for f in synth.frame_set(wl, t, device="cpu")]
+
+
+def time_oracle(wl, args, seconds, threads):
+    """Run the oracle over frame sets of `wl` (rows cut so that the run takes
+    about `seconds`); returns (Mpix/s, sample description)."""
+    import oracle
+    from oracle import core
+    oracle.build()
+    p = core.Params(fit_mode=0 if args.fit == "global" else 1, num_blocks=1 if args.fit == "global" else 16,
+                    schedule=0 if args.schedule == "current" else 1)
+    Hmin = min(c.height for c in wl.cams)
+    # calibrate on a 64-row cut
+    cal = cpu_rows_sample(wl, 64)
+    fr = oracle_frames_host(cal, 0)
+    o = core.ArrayOracle(cal.cams, p, threads=threads)
+    t0 = time.perf_counter()
+    o.step(fr)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    per_row = dt / 64
+    rows = int(min(Hmin, max(2, seconds / 3 / per_row)))
+    rows -= rows % 2
+    samp = cpu_rows_sample(wl, rows)
+    frames = [oracle_frames_host(samp, t) for t in range(3)]
+    o = core.ArrayOracle(samp.cams, p, threads=threads)
+    t0 = time.perf_counter()
+    for f in frames:
+        o.step(f)
+    el = time.perf_counter() - t0
+    px = 3 * sum(c.width * c.height for c in samp.cams)
+    desc = "3 frame sets of the array cut to its first %d rows (%d px per set), %d threads over cameras" % (
+        rows, px // 3, threads)
+    return px / el / 1e6, desc, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args.workload)
+    threads = max(1, min(len(wl.cams), os.cpu_count() or 1))
+    import oracle
+    from oracle import core
+    oracle.build()
+    p = core.Params(fit_mode=0 if args.fit == "global" else 1, num_blocks=1 if args.fit == "global" else 16,
+                    schedule=0 if args.schedule == "current" else 1)
+    total = args.steps + args.warmup
+    # each step: one frame set of the array cut to R rows, R sized so the run takes ~2 minutes
+    cal = cpu_rows_sample(wl, 16)
+    fr = oracle_frames_host(cal, 0)
+    o = core.ArrayOracle(cal.cams, p, threads=threads)
+    t0 = time.perf_counter()
+    o.step(fr)
+    per_row = max(time.perf_counter() - t0, 1e-4) / 16
+    Hmin = min(c.height for c in wl.cams)
+    rows = int(min(Hmin, max(2, 120.0 / total / per_row)))
+    rows -= rows % 2
+    samp = cpu_rows_sample(wl, rows)
+    frames = [oracle_frames_host(samp, t) for t in range(2)]
+    o = core.ArrayOracle(samp.cams, p, threads=threads)
+    for i in range(args.warmup):
+        o.step(frames[i % 2])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        o.step(frames[i % 2])
+    el = time.perf_counter() - t0
+    px = sum(c.width * c.height for c in samp.cams)
+    value = px * args.steps / el / 1e6
+    line = {
+        "impl": "reference", "metric": json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"],
+        "value": value, "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": config_dict(args, wl, "CPU: two frame sets alternating"),
+        "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": threads, "kind": "oracle",
+                         "sample": "each step one frame set of the array cut to its first %d rows (%d px)" % (rows, px)},
+        "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1910_03517_gb300 import rt, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = workload(args.workload)
+    K, W = args.steps, args.warmup
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    in_bytes = input_bytes(wl)
+    ring = args.ring or max(6, -(-int(4 * l2 / in_bytes + 1) // 6) * 6)
+    ring = max(6, ring - ring % 6)
+    # the ring of distinct input frame sets, resident in HBM
+    frames = [synth.frame_set(wl, t, device=dev) for t in range(ring)]
+    crops = [synth.crop_list(wl, t) for t in range(ring)] if wl.n_crops else None
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    arr = rt.CameraArray(wl.cams, stream=stream, **array_kwargs(args, wl))
+
+    t_sub = [0]
+
+    def submit_one():
+        i = t_sub[0] % ring
+        arr.submit_frames(frames[i], t_sub[0], crops[i] if crops else ())
+        t_sub[0] += 1
+
+    # Warm-up: W frame sets.  Frame set 0 starts the sequence; the graph over
+    # the ring is captured (with profiling events inside) at the ring position
+    # where the timed region will start, and launched once in the warm-up when
+    # W leaves room for a whole ring.
+    warm_graph = W - 1 >= ring
+    singles = (W - 1 - ring) if warm_graph else (W - 1)
+    for _ in range(1 + max(0, singles)):
+        submit_one()
+    arr.sync()
+    arr.profile(True)
+    order = [(t_sub[0] + j) % ring for j in range(ring)]
+    arr.capture_sequence([frames[i] for i in order], [crops[i] for i in order] if crops else None)
+    arr.profile(False)
+    if warm_graph:
+        arr.launch_sequence()
+        t_sub[0] += ring
+    arr.sync()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K // ring):
+        arr.launch_sequence()
+        t_sub[0] += ring
+    for _ in range(K % ring):
+        submit_one()
+    arr.stream_wait(stream)
+    e1.record(stream)
+    e1.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        if world > 1:
+            dist.barrier()
+    prof = arr.get_profile()
+    arr.profile(False)
+    px_set = wl.pixels
+    value = world * K * px_set / (ms / 1e3) / 1e6
+    # roofline of the dominant kernel, pass B
+    peak, peak_kind = measured_peak()
+    pb_ms = prof["pass_b_ms"] / max(1, prof["frame_sets"])
+    ab = alg_bytes(wl)
+    achieved = ab / (pb_ms / 1e3) / 1e9 if pb_ms > 0 else None
+    traffic = ncu_traffic(args.workload)
+    launches_per_set = 3 + (1 if wl.n_crops else 0)
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    ke = max(6, min(args.e2e_steps, K))
+    if rank == 0 or world > 1:
+        nh = 3
+        host = [[{k: v.cpu().pin_memory() for k, v in f.items()} for f in frames[i]] for i in range(nh)]
+        opitch = 3 * max(c.width for c in wl.cams)
+        outs = [[torch.empty((c.height, opitch), dtype=torch.uint8).pin_memory() for c in wl.cams]
+                for _ in range(2)]
+        arr2 = rt.CameraArray(wl.cams, stream=stream, **array_kwargs(args, wl))
+        for i in range(3):
+            arr2.submit_frames_host(host[i % nh], i, crops[i % ring] if crops else (), rgb_out=outs[i % 2],
+                                    rgb_out_pitch=opitch)
+        arr2.sync()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for i in range(ke):
+            t = 3 + i
+            # outputs of frame set t land in outs[t % 2]; it was last written by t-2, done before t's copy
+            arr2.submit_frames_host(host[t % nh], t, crops[t % ring] if crops else (), rgb_out=outs[t % 2],
+                                    rgb_out_pitch=opitch)
+        arr2.stream_wait(stream)
+        s1.record(stream)
+        s1.synchronize()
+        ems = s0.elapsed_time(s1)
+        h2d = in_bytes
+        d2h = sum(3 * c.width * c.height for c in wl.cams)
+        e2e = {"value": world * ke * px_set / (ems / 1e3) / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": ke}
+        arr2.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = max(1, min(len(wl.cams), os.cpu_count() or 1))
+        v, desc, el = time_oracle(wl, args, args.cpu_seconds, threads)
+        cpu = {"value": v, "unit": "Mpix/s", "cores": threads, "kind": "oracle", "sample": desc,
+               "seconds": round(el, 2)}
+
+    arr.close()
+    if rank == 0:
+        base = json.load(open(os.path.join(ROOT, "BASELINE.json")))
+        ring_desc = "ring of %d distinct input frame sets (%.0f MB) > 4x L2 (%.0f MB); outputs double buffered" % (
+            ring, ring * in_bytes / 1e6, l2 / 1e6)
+        line = {
+            "metric": base["metric"], "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": config_dict(args, wl, ring_desc),
+            "array_fps": world * K / (ms / 1e3),
+            "hbm_frac_whole_step": (world * K * ab / (ms / 1e3) / 1e9) / peak / world,
+            "roofline": {"bound": "hbm", "kernel": "pass_b (convert + frame histograms + Q16 apply)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                         "traffic": traffic, "alg_bytes_per_launch": ab,
+                         "pass_ms_per_set": {"pass_a": prof["pass_a_ms"] / max(1, prof["frame_sets"]),
+                                             "solve": prof["solve_ms"] / max(1, prof["frame_sets"]),
+                                             "pass_b": pb_ms,
+                                             "crops": prof["crops_ms"] / max(1, prof["frame_sets"])},
+                         "timed_frame_sets": prof["frame_sets"]},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": K * launches_per_set,
+            "clocks": ck,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,144 @@
+// Pass A: the measured spectra of Sec. "White balance and exposure
+// correction" -- per camera, band side (first / last S columns), vertical
+// block and channel, the histogram of the band's converted RGB values, with
+// (i) moving pixels removed: |Y_t - Y_{t-1}| > T on the band's luma
+// (object removal, Fig. "thresholded difference"; the first frame set of a
+// sequence has no previous frame and removes nothing), and (ii) saturated
+// values 0 and 255 left out per channel.  Counts, sums and sums of squares
+// are the histogram's moments, reduced from it at the end of every CTA.
+//
+// One CTA per work item (camera, side, rows inside one block); a thread
+// converts 16 band pixels of one row per iteration with one 16-byte load of
+// Y (plus one of UV) and one of the previous frame's band luma, and writes
+// this frame's band luma for the next frame set.
+#include "rt_internal.cuh"
+#include "pixel.cuh"
+
+namespace rt {
+
+namespace {
+
+__device__ __forceinline__ uint4 ld16(const uint8_t *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
+
+// 16 bytes at any address: one vector load when 16-byte aligned, else byte
+// loads (the right band starts at W - S, unaligned when W is not a multiple
+// of 16; only such ragged cameras take this path).
+__device__ __forceinline__ uint4 ld16_any(const uint8_t *p)
+{
+    if (((uintptr_t)p & 15u) == 0) return ld16(p);
+    uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 16; ++i) w[i >> 2] |= (uint32_t)__ldg(p + i) << (8 * (i & 3));
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const PassAArgs a, int Hmax)
+{
+    __shared__ uint32_t sh[3 * 256];
+    const StripItem it = a.items[blockIdx.x];
+    const CamGeom &cg = g.cam[it.cam];
+    const ConvConsts k = conv_consts(g.matrix);
+    for (int i = threadIdx.x; i < 768; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+
+    const int upr = a.S / kUnitCols;
+    const int xb = it.side == 0 ? 0 : cg.W - a.S;
+    const int nrows = it.row1 - it.row0;
+    const size_t lbase = (size_t)it.cam * a.luma_cam_stride + (size_t)it.side * Hmax * a.S;
+    for (int u = threadIdx.x; u < nrows * upr; u += blockDim.x) {
+        const int y = it.row0 + u / upr;
+        const int x0 = xb + (u % upr) * kUnitCols;
+        uint32_t luma[4];
+        uint32_t vb[16][3];
+        if (cg.fmt == RT_NV12) {
+            const uint4 Y = ld16_any(cg.y + (size_t)y * cg.y_pitch + x0);
+            const uint4 UV = ld16_any(cg.uv + (size_t)(y >> 1) * cg.uv_pitch + x0);
+            luma[0] = Y.x; luma[1] = Y.y; luma[2] = Y.z; luma[3] = Y.w;
+            const uint32_t uvw[4] = {UV.x, UV.y, UV.z, UV.w};
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const float Uf = byte_f(uvw[p >> 1], (p & 1) * 2);
+                const float Vf = byte_f(uvw[p >> 1], (p & 1) * 2 + 1);
+                const float cz[3] = {fmaf(Vf, k.krv, k.c_r0), fmaf(Uf, k.kgu, fmaf(Vf, k.kgv, k.c_g0)),
+                                     fmaf(Uf, k.kbu, k.c_b0)};
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int i = 2 * p + q;
+                    const float Yf = byte_f(luma[i >> 2], i & 3);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) vb[i][c] = zbits(Yf, k.ky, cz[c]);
+                }
+            }
+        } else {
+            const uint8_t *p = cg.y + (size_t)y * cg.y_pitch + 2 * x0;
+            const uint4 A = ld16_any(p), Bv = ld16_any(p + 16);
+            const uint32_t w[8] = {A.x, A.y, A.z, A.w, Bv.x, Bv.y, Bv.z, Bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) luma[i] = 0;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const uint32_t b = mono_bits((w[i >> 1] >> (16 * (i & 1))) & 0xFFFFu, cg.shift);
+                vb[i][0] = vb[i][1] = vb[i][2] = b;
+                luma[i >> 2] |= (b - kMagicBits) << (8 * (i & 3));
+            }
+        }
+        const size_t lo = lbase + (size_t)y * a.S + (x0 - xb);
+        *reinterpret_cast<uint4 *>(a.cur_luma + lo) = make_uint4(luma[0], luma[1], luma[2], luma[3]);
+        uint32_t prev[4] = {luma[0], luma[1], luma[2], luma[3]};
+        if (!a.first) {
+            const uint4 P = ld16(a.prev_luma + lo);
+            prev[0] = P.x; prev[1] = P.y; prev[2] = P.z; prev[3] = P.w;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int d = (int)((luma[i >> 2] >> (8 * (i & 3))) & 255u) - (int)((prev[i >> 2] >> (8 * (i & 3))) & 255u);
+            if (d > a.T || d < -a.T) continue;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const uint32_t v = vb[i][c] - kMagicBits;
+                if (v == 0u || v == 255u) continue;
+                atomicAdd(&sh[c * 256 + v], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    const size_t slot = ((size_t)(it.cam * 2 + it.side) * g.B + it.block) * 3;
+    for (int b = threadIdx.x; b < 768; b += blockDim.x) {
+        const uint32_t cnt = sh[b];
+        if (cnt) atomicAdd(a.hist + slot * 256 + b, cnt);
+    }
+    // moments of the three channel histograms: warp c reduces channel c
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 3) {
+        unsigned long long n = 0, s = 0, ss = 0;
+        for (int b = lane; b < 256; b += 32) {
+            const unsigned long long cnt = sh[warp * 256 + b];
+            n += cnt;
+            s += cnt * (unsigned long long)b;
+            ss += cnt * (unsigned long long)(b * b);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            n += __shfl_xor_sync(0xffffffffu, n, o);
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        }
+        if (lane == 0 && n) {
+            atomicAdd(a.n + slot + warp, (uint32_t)n);
+            atomicAdd(a.sum + slot + warp, s);
+            atomicAdd(a.sumsq + slot + warp, ss);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pass_a(const ArrayGeom &g, const PassAArgs &a, int threads, cudaStream_t s)
+{
+    if (a.n_items == 0) return cudaSuccess;
+    const int Hmax = a.luma_cam_stride / (2 * a.S);
+    pass_a_kernel<<<a.n_items, threads, 0, s>>>(g, a, Hmax);
+    return cudaGetLastError();
+}
+
+}  // namespace rt

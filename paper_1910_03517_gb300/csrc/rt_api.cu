@@ -1,0 +1,1005 @@
+// Host runtime of librt.so: the C ABI declared in include/rt.h.
+//
+// Pipelining.  Per frame set t the library enqueues
+//   stats stream (high priority):  pass A(t) -> solve(t)          [latency bound, small]
+//   main stream:                   clear(t) -> pass B(t) -> crops(t)  [bandwidth bound]
+// with pass B(t) waiting for solve(t) (current schedule) or solve(t-1)
+// (lagged schedule).  Pass A / solve of frame set t+1 therefore run while
+// pass B of frame set t streams through HBM, and the latency of the tiny
+// statistics chain hides behind the bandwidth-bound pass.  Buffers written
+// per frame set are double buffered (outputs, histograms, band luma) and the
+// Q16 table is a ring of three; before frame set t reuses a slot the stats
+// stream waits for pass B(t-2) to have finished.
+//
+// Every wait the host does is bounded (rt_get_*, rt_sync: cudaEventQuery
+// polling with a deadline), and no kernel waits on another.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "rt_internal.cuh"
+
+using namespace rt;
+
+namespace {
+
+constexpr int kEvRing = 4;
+constexpr int kQRing = 3;
+constexpr int kStripRows = 64;      // rows of one pass-A work item
+constexpr uint32_t kStateMagic = 0x52545331u;
+constexpr int kMaxProfiled = 4096;  // frame sets whose pass times one collection keeps
+
+// CUDA events around the passes of one frame set (profiling)
+struct ProfEv {
+    cudaEvent_t a0, a1, s1, b0, b1, c1;
+    bool crops;
+};
+
+thread_local std::string g_config_error;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct rt_handle {
+    rt_array_params p{};
+    std::vector<rt_camera_desc> cams;
+    int dev = 0, sm_count = 0;
+    cudaStream_t user = nullptr, s_stats = nullptr, s_main = nullptr, s_copy = nullptr, s_d2h = nullptr;
+    ArrayGeom geom{};
+    int Hmax = 0;
+    // outputs and statistics
+    uint8_t *rgb[2] = {nullptr, nullptr};
+    std::vector<size_t> rgb_off;
+    size_t rgb_bytes = 0;
+    uint32_t *frame_hist[2] = {nullptr, nullptr};
+    uint32_t *strip_hist[2] = {nullptr, nullptr};
+    uint32_t *strip_n[2] = {nullptr, nullptr};
+    unsigned long long *strip_sum[2] = {nullptr, nullptr}, *strip_sumsq[2] = {nullptr, nullptr};
+    uint8_t *luma[2] = {nullptr, nullptr};
+    size_t luma_cam_stride = 0;
+    double *maps_new = nullptr, *E = nullptr;
+    int32_t *q16[kQRing] = {nullptr, nullptr, nullptr};
+    int32_t *q16_identity = nullptr;
+    int32_t *ramp = nullptr;
+    StripItem *items = nullptr;
+    int n_items = 0;
+    int32_t *group_start = nullptr, *group_members = nullptr, *left_nbr = nullptr, *right_nbr = nullptr,
+            *cam_H = nullptr;
+    int n_groups = 0;
+    __half *crops[2] = {nullptr, nullptr};
+    rt_crop *crop_dev[2] = {nullptr, nullptr};
+    rt_crop *crop_host = nullptr;          // pinned [2][max_crops]
+    int n_crops[2] = {0, 0};
+    // host-input staging
+    uint8_t *stage[2] = {nullptr, nullptr};
+    std::vector<size_t> stage_y_off, stage_uv_off;
+    size_t stage_bytes = 0;
+    // events
+    cudaEvent_t ev_user = nullptr, ev_in = nullptr, ev_tmp = nullptr;
+    cudaEvent_t ev_solved[kEvRing] = {}, ev_done[kEvRing] = {}, ev_out[kEvRing] = {};
+    bool launched[kEvRing] = {}, out_launched[kEvRing] = {};
+    int64_t t = 0;                 // frame sets submitted
+    bool restart = true;           // next submit starts a sequence
+    bool last_first = true;        // the last frame set started its sequence
+    // profiling
+    bool prof_on = false;
+    std::vector<ProfEv> prof, cap_prof;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_pool_used = 0;
+    bool last_was_graph = false;
+    bool graph_launched = false;   // the captured graph ran since profiling started
+    // captured sequence
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int cap_n = 0;
+    int64_t cap_t0 = 0;
+    bool capturing = false;
+    rt_crop *cap_crops = nullptr;
+    size_t cap_crops_n = 0;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // pass B launch shape
+    int pb_grid = 0, pb_threads = 512;
+    size_t pb_smem = 0;
+    std::string err;
+    size_t n_maps = 0;             // K*2*B*3*2
+};
+
+namespace {
+
+rt_status fail(rt_handle *h, rt_status s, const std::string &msg)
+{
+    if (h) h->err = msg;
+    else g_config_error = msg;
+    return s;
+}
+
+rt_status cuda_fail(rt_handle *h, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, m);
+}
+
+#define RT_CUDA(h, call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+rt_status wait_event(rt_handle *h, cudaEvent_t ev, int32_t timeout_ms)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return RT_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(h, e, "cudaEventQuery");
+        if (timeout_ms >= 0) {
+            auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+            if (ms >= timeout_ms) return fail(h, RT_ERR_TIMEOUT, "timed out waiting for the GPU");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+template <class T>
+rt_status dalloc(rt_handle *h, T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) return RT_OK;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+    e = cudaMemset(*p, 0, n * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset");
+    return RT_OK;
+}
+
+rt_status validate(const rt_array_params *p)
+{
+    if (!p || !p->cams) return fail(nullptr, RT_ERR_INVALID, "params or cams is NULL");
+    if (p->num_cameras < 1 || p->num_cameras > RT_MAX_CAMERAS)
+        return fail(nullptr, RT_ERR_INVALID, "num_cameras must be in 1..32");
+    if (p->strip_width < 16 || p->strip_width % 16)
+        return fail(nullptr, RT_ERR_INVALID, "strip_width must be a positive multiple of 16");
+    if (p->num_blocks < 1 || p->num_blocks > RT_MAX_BLOCKS)
+        return fail(nullptr, RT_ERR_INVALID, "num_blocks must be in 1..64");
+    if (p->fit_mode != RT_FIT_GLOBAL && p->fit_mode != RT_FIT_SEAM_AFFINE)
+        return fail(nullptr, RT_ERR_INVALID, "bad fit_mode");
+    if (p->schedule != RT_SCHED_CURRENT && p->schedule != RT_SCHED_LAGGED)
+        return fail(nullptr, RT_ERR_INVALID, "bad schedule");
+    if (p->topology != RT_LINEAR && p->topology != RT_RING) return fail(nullptr, RT_ERR_INVALID, "bad topology");
+    if (p->color_matrix != RT_BT709 && p->color_matrix != RT_BT601)
+        return fail(nullptr, RT_ERR_INVALID, "bad color_matrix");
+    if (p->motion_threshold < 0 || p->motion_threshold > 255)
+        return fail(nullptr, RT_ERR_INVALID, "motion_threshold must be in 0..255");
+    if (p->min_valid < 1) return fail(nullptr, RT_ERR_INVALID, "min_valid must be >= 1");
+    if (!(p->alpha > 0.0 && p->alpha <= 1.0)) return fail(nullptr, RT_ERR_INVALID, "alpha must be in (0, 1]");
+    if (!(p->lambda > 0.0)) return fail(nullptr, RT_ERR_INVALID, "lambda must be > 0");
+    if (!(p->gain_min > 0.0 && p->gain_min <= 1.0 && p->gain_max >= 1.0 && p->gain_max <= 16.0))
+        return fail(nullptr, RT_ERR_INVALID, "need 0 < gain_min <= 1 <= gain_max <= 16");
+    if (p->max_crops < 0 || p->max_crops > 4096) return fail(nullptr, RT_ERR_INVALID, "max_crops must be in 0..4096");
+    if (p->max_crops > 0 && (p->crop_size < 1 || p->crop_size > 4096))
+        return fail(nullptr, RT_ERR_INVALID, "crop_size must be in 1..4096");
+    if (p->flags & ~(RT_FLAG_FRAME_STATS)) return fail(nullptr, RT_ERR_INVALID, "unsupported flags");
+    unsigned long long units = 0;
+    for (int k = 0; k < p->num_cameras; ++k) {
+        const rt_camera_desc &c = p->cams[k];
+        char buf[160];
+        if (c.format != RT_NV12 && c.format != RT_MONO16) {
+            snprintf(buf, sizeof buf, "camera %d: bad format", k);
+            return fail(nullptr, RT_ERR_INVALID, buf);
+        }
+        if (c.width < 2 * p->strip_width || c.width % 2 || c.height < 2 || c.height % 2 || c.width > 16384 ||
+            c.height > 16384) {
+            snprintf(buf, sizeof buf, "camera %d: width and height must be even, width >= 2*strip_width", k);
+            return fail(nullptr, RT_ERR_INVALID, buf);
+        }
+        if (c.height < p->num_blocks) {
+            snprintf(buf, sizeof buf, "camera %d: fewer rows than blocks", k);
+            return fail(nullptr, RT_ERR_INVALID, buf);
+        }
+        const int bpp = c.format == RT_MONO16 ? 2 : 1;
+        if (c.y_pitch % 16 || c.y_pitch < (int)align_up((size_t)c.width * bpp, 16)) {
+            snprintf(buf, sizeof buf, "camera %d: y_pitch must be a multiple of 16 >= the row bytes rounded up to 16", k);
+            return fail(nullptr, RT_ERR_INVALID, buf);
+        }
+        if (c.format == RT_NV12 && (c.uv_pitch % 16 || c.uv_pitch < (int)align_up((size_t)c.width, 16))) {
+            snprintf(buf, sizeof buf, "camera %d: uv_pitch must be a multiple of 16 >= width rounded up to 16", k);
+            return fail(nullptr, RT_ERR_INVALID, buf);
+        }
+        if (c.format == RT_MONO16 && (c.bit_depth < 8 || c.bit_depth > 16)) {
+            snprintf(buf, sizeof buf, "camera %d: bit_depth must be in 8..16", k);
+            return fail(nullptr, RT_ERR_INVALID, buf);
+        }
+        if (c.group < 0) return fail(nullptr, RT_ERR_INVALID, "group must be >= 0");
+        for (int q = 0; q < k; ++q)
+            if (p->cams[q].group == c.group && p->cams[q].position == c.position)
+                return fail(nullptr, RT_ERR_INVALID, "two cameras share a group and a position");
+        units += (unsigned long long)(c.height / 2) * ((c.width + 15) / 16);
+    }
+    if (units >= (1ull << 31)) return fail(nullptr, RT_ERR_INVALID, "array too large");
+    return RT_OK;
+}
+
+void free_all(rt_handle *h)
+{
+    auto F = [](void *p) { if (p) cudaFree(p); };
+    for (int i = 0; i < 2; ++i) {
+        F(h->rgb[i]); F(h->frame_hist[i]); F(h->strip_hist[i]); F(h->strip_sum[i]);
+        F(h->luma[i]); F(h->crops[i]); F(h->crop_dev[i]); F(h->stage[i]);
+    }
+    for (int i = 0; i < kQRing; ++i) F(h->q16[i]);
+    F(h->maps_new); F(h->E); F(h->q16_identity); F(h->ramp); F(h->items); F(h->group_start);
+    F(h->group_members); F(h->left_nbr); F(h->right_nbr); F(h->cam_H);
+    if (h->crop_host) cudaFreeHost(h->crop_host);
+    cudaStream_t ss[] = {h->s_stats, h->s_main, h->s_copy, h->s_d2h};
+    for (auto s : ss) if (s) cudaStreamDestroy(s);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    F(h->cap_crops);
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    cudaEvent_t ee[] = {h->ev_user, h->ev_in, h->ev_tmp, h->ev_fork, h->ev_join};
+    for (auto e : ee) if (e) cudaEventDestroy(e);
+    for (int i = 0; i < kEvRing; ++i) {
+        if (h->ev_solved[i]) cudaEventDestroy(h->ev_solved[i]);
+        if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
+        if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
+    }
+}
+
+rt_status setup(rt_handle *h)
+{
+    const rt_array_params &p = h->p;
+    const int K = p.num_cameras, B = p.num_blocks, S = p.strip_width;
+    RT_CUDA(h, cudaGetDevice(&h->dev));
+    RT_CUDA(h, cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->dev));
+    int lo = 0, hi = 0;
+    RT_CUDA(h, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_stats, cudaStreamNonBlocking, hi));
+    RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_main, cudaStreamNonBlocking, lo));
+    RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking));
+    RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_d2h, cudaStreamNonBlocking));
+    RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_user, cudaEventDisableTiming));
+    RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_tmp, cudaEventDisableTiming));
+    RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    for (int i = 0; i < kEvRing; ++i) {
+        RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_solved[i], cudaEventDisableTiming));
+        RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming));
+        RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming));
+    }
+
+    // geometry, outputs
+    ArrayGeom &g = h->geom;
+    memset(&g, 0, sizeof g);
+    g.K = K; g.B = B; g.fit_mode = p.fit_mode; g.matrix = p.color_matrix;
+    h->rgb_off.resize(K);
+    size_t off = 0;
+    uint32_t units = 0;
+    h->Hmax = 0;
+    for (int k = 0; k < K; ++k) {
+        const rt_camera_desc &c = h->cams[k];
+        CamGeom &cg = g.cam[k];
+        cg.W = c.width; cg.H = c.height; cg.y_pitch = c.y_pitch; cg.uv_pitch = c.uv_pitch;
+        cg.rgb_pitch = (int)align_up((size_t)3 * c.width, 16);
+        cg.fmt = c.format; cg.shift = c.format == RT_MONO16 ? c.bit_depth - 8 : 0;
+        cg.upr = (uint32_t)((c.width + 15) / 16);
+        cg.unit_base = units;
+        units += cg.upr * (uint32_t)(c.height / 2);
+        h->rgb_off[k] = off;
+        off += align_up((size_t)cg.rgb_pitch * c.height, 256);
+        h->Hmax = std::max(h->Hmax, c.height);
+    }
+    g.units_total = units;
+    h->rgb_bytes = off;
+    for (int i = 0; i < 2; ++i) {
+        rt_status s;
+        if ((s = dalloc(h, &h->rgb[i], off)) != RT_OK) return s;
+        if ((s = dalloc(h, &h->frame_hist[i], (size_t)K * 768)) != RT_OK) return s;
+        // histograms and counts in one allocation, sums and sums of squares in
+        // another, so that the solve clears a slot with two ranges
+        const size_t nb = (size_t)K * 2 * B;
+        if ((s = dalloc(h, &h->strip_hist[i], nb * 768 + nb * 3)) != RT_OK) return s;
+        h->strip_n[i] = h->strip_hist[i] + nb * 768;
+        if ((s = dalloc(h, &h->strip_sum[i], nb * 3 * 2)) != RT_OK) return s;
+        h->strip_sumsq[i] = h->strip_sum[i] + nb * 3;
+        h->luma_cam_stride = (size_t)2 * h->Hmax * S;
+        if ((s = dalloc(h, &h->luma[i], (size_t)K * h->luma_cam_stride)) != RT_OK) return s;
+        if (p.max_crops > 0) {
+            if ((s = dalloc(h, &h->crops[i], (size_t)p.max_crops * 3 * p.crop_size * p.crop_size)) != RT_OK) return s;
+            if ((s = dalloc(h, &h->crop_dev[i], (size_t)p.max_crops)) != RT_OK) return s;
+        }
+    }
+    if (p.max_crops > 0) RT_CUDA(h, cudaMallocHost((void **)&h->crop_host, sizeof(rt_crop) * 2 * p.max_crops));
+    h->n_maps = (size_t)K * 2 * B * 3 * 2;
+    rt_status s;
+    if ((s = dalloc(h, &h->maps_new, h->n_maps)) != RT_OK) return s;
+    if ((s = dalloc(h, &h->E, h->n_maps)) != RT_OK) return s;
+    for (int i = 0; i < kQRing; ++i)
+        if ((s = dalloc(h, &h->q16[i], h->n_maps)) != RT_OK) return s;
+    if ((s = dalloc(h, &h->q16_identity, h->n_maps)) != RT_OK) return s;
+    {
+        std::vector<int32_t> id(h->n_maps);
+        for (size_t i = 0; i < h->n_maps; ++i) id[i] = (i % 2 == 0) ? 65536 : 0;
+        RT_CUDA(h, cudaMemcpy(h->q16_identity, id.data(), id.size() * 4, cudaMemcpyHostToDevice));
+    }
+    // Q16 ramp weight per column, for the seam maps
+    {
+        std::vector<int32_t> rmp;
+        std::vector<size_t> roff(K);
+        for (int k = 0; k < K; ++k) {
+            roff[k] = rmp.size();
+            const long long W = h->cams[k].width, half = W / 2;
+            for (long long x = 0; x < W; ++x)
+                rmp.push_back((int32_t)(x < half ? ((half - x) * 65536) / half : ((x - half + 1) * 65536) / half));
+        }
+        if ((s = dalloc(h, &h->ramp, rmp.size())) != RT_OK) return s;
+        RT_CUDA(h, cudaMemcpy(h->ramp, rmp.data(), rmp.size() * 4, cudaMemcpyHostToDevice));
+        for (int k = 0; k < K; ++k) g.cam[k].ramp = h->ramp + roff[k];
+    }
+    // pass A work items: (camera, side, block) rows split into chunks
+    {
+        std::vector<StripItem> items;
+        for (int k = 0; k < K; ++k)
+            for (int side = 0; side < 2; ++side)
+                for (int j = 0; j < B; ++j) {
+                    const int H = h->cams[k].height;
+                    const int r0 = (int)(((long long)j * H) / B), r1 = (int)(((long long)(j + 1) * H) / B);
+                    for (int r = r0; r < r1; r += kStripRows) {
+                        StripItem it;
+                        it.cam = (int16_t)k; it.side = (int16_t)side; it.block = (int16_t)j; it.pad = 0;
+                        it.row0 = r; it.row1 = std::min(r1, r + kStripRows);
+                        items.push_back(it);
+                    }
+                }
+        h->n_items = (int)items.size();
+        if ((s = dalloc(h, &h->items, items.size())) != RT_OK) return s;
+        RT_CUDA(h, cudaMemcpy(h->items, items.data(), items.size() * sizeof(StripItem), cudaMemcpyHostToDevice));
+    }
+    // seam chains
+    {
+        std::vector<int> groups;
+        for (auto &c : h->cams) if (std::find(groups.begin(), groups.end(), c.group) == groups.end()) groups.push_back(c.group);
+        std::sort(groups.begin(), groups.end());
+        std::vector<int32_t> gs(1, 0), gm, ln(K, -1), rn(K, -1), hh(K);
+        for (int gid : groups) {
+            std::vector<int> m;
+            for (int k = 0; k < K; ++k) if (h->cams[k].group == gid) m.push_back(k);
+            std::sort(m.begin(), m.end(), [&](int a, int b) { return h->cams[a].position < h->cams[b].position; });
+            for (size_t i = 0; i < m.size(); ++i) {
+                gm.push_back(m[i]);
+                if (i + 1 < m.size()) { rn[m[i]] = m[i + 1]; ln[m[i + 1]] = m[i]; }
+            }
+            if (h->p.topology == RT_RING && m.size() >= 2) { rn[m.back()] = m.front(); ln[m.front()] = m.back(); }
+            gs.push_back((int32_t)gm.size());
+        }
+        for (int k = 0; k < K; ++k) hh[k] = h->cams[k].height;
+        h->n_groups = (int)groups.size();
+        if ((s = dalloc(h, &h->group_start, gs.size())) != RT_OK) return s;
+        if ((s = dalloc(h, &h->group_members, gm.size())) != RT_OK) return s;
+        if ((s = dalloc(h, &h->left_nbr, (size_t)K)) != RT_OK) return s;
+        if ((s = dalloc(h, &h->right_nbr, (size_t)K)) != RT_OK) return s;
+        if ((s = dalloc(h, &h->cam_H, (size_t)K)) != RT_OK) return s;
+        RT_CUDA(h, cudaMemcpy(h->group_start, gs.data(), gs.size() * 4, cudaMemcpyHostToDevice));
+        RT_CUDA(h, cudaMemcpy(h->group_members, gm.data(), gm.size() * 4, cudaMemcpyHostToDevice));
+        RT_CUDA(h, cudaMemcpy(h->left_nbr, ln.data(), ln.size() * 4, cudaMemcpyHostToDevice));
+        RT_CUDA(h, cudaMemcpy(h->right_nbr, rn.data(), rn.size() * 4, cudaMemcpyHostToDevice));
+        RT_CUDA(h, cudaMemcpy(h->cam_H, hh.data(), hh.size() * 4, cudaMemcpyHostToDevice));
+    }
+    // pass B launch shape: a persistent grid of all resident CTAs
+    RT_CUDA(h, pass_b_prepare(h->pb_threads, &h->pb_smem));
+    h->pb_grid = h->sm_count * 2;
+    RT_CUDA(h, cudaDeviceSynchronize());
+    return RT_OK;
+}
+
+rt_status check_crops(rt_handle *h, const rt_crop *crops, int32_t n)
+{
+    if (n < 0 || n > h->p.max_crops) return fail(h, RT_ERR_INVALID, "n_crops out of range");
+    if (n > 0 && !crops) return fail(h, RT_ERR_INVALID, "crops is NULL");
+    for (int i = 0; i < n; ++i) {
+        const rt_crop &c = crops[i];
+        if (c.cam < 0 || c.cam >= h->p.num_cameras) return fail(h, RT_ERR_INVALID, "crop camera out of range");
+        const rt_camera_desc &d = h->cams[c.cam];
+        if (c.w < 1 || c.h < 1 || c.x0 < 0 || c.y0 < 0 || c.x0 + c.w > d.width || c.y0 + c.h > d.height)
+            return fail(h, RT_ERR_INVALID, "crop window outside its camera");
+    }
+    return RT_OK;
+}
+
+rt_status pool_event(rt_handle *h, cudaEvent_t *e)
+{
+    if (h->ev_pool_used == h->ev_pool.size()) {
+        cudaEvent_t ev;
+        RT_CUDA(h, cudaEventCreate(&ev));
+        h->ev_pool.push_back(ev);
+    }
+    *e = h->ev_pool[h->ev_pool_used++];
+    return RT_OK;
+}
+
+// Enqueue one frame set whose planes are device addresses in y[] / uv[].
+// While a sequence is being captured (h->capturing) nothing waits on the host
+// and the crops come from crop_table, uploaded before the capture.
+rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int64_t frame_index,
+                  const rt_crop *crops, int32_t n_crops, bool inputs_on_copy_stream,
+                  const rt_crop *crop_table = nullptr)
+{
+    const rt_array_params &p = h->p;
+    const int K = p.num_cameras;
+    const int64_t t = h->t;
+    const int par = (int)(t & 1), ev = (int)(t % kEvRing), qs = (int)(t % kQRing);
+    const bool first = h->restart || frame_index == 0;
+
+    ArrayGeom g = h->geom;
+    for (int k = 0; k < K; ++k) {
+        g.cam[k].y = static_cast<const uint8_t *>(y[k]);
+        g.cam[k].uv = static_cast<const uint8_t *>(uv ? uv[k] : nullptr);
+        g.cam[k].rgb = h->rgb[par] + h->rgb_off[k];
+    }
+    // inputs become ready on the caller's stream (or the copy stream)
+    if (!h->capturing) {
+        if (inputs_on_copy_stream) {
+            RT_CUDA(h, cudaEventRecord(h->ev_in, h->s_copy));
+        } else {
+            RT_CUDA(h, cudaEventRecord(h->ev_in, h->user));
+        }
+        RT_CUDA(h, cudaStreamWaitEvent(h->s_stats, h->ev_in, 0));
+        RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_in, 0));
+    }
+    const int ev2 = (int)((t + kEvRing - 2) % kEvRing);
+    const bool dep2 = h->capturing ? (t - 2 >= h->cap_t0) : (t >= 2 && h->launched[ev2]);
+    if (dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_stats, h->ev_done[ev2], 0));
+    if (!h->capturing && t >= 2 && h->out_launched[ev2])
+        RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_out[ev2], 0));
+    ProfEv pe{};
+    const bool prof = h->prof_on && (h->capturing || h->prof.size() < (size_t)kMaxProfiled);
+    if (prof) {
+        rt_status s;
+        cudaEvent_t *evs[] = {&pe.a0, &pe.a1, &pe.s1, &pe.b0, &pe.b1, &pe.c1};
+        for (auto e : evs)
+            if ((s = pool_event(h, e)) != RT_OK) return s;
+        RT_CUDA(h, cudaEventRecord(pe.a0, h->s_stats));
+    }
+    // statistics chain: pass A -> solve
+    PassAArgs pa{};
+    pa.items = h->items; pa.n_items = h->n_items; pa.S = p.strip_width; pa.T = p.motion_threshold;
+    pa.first = first ? 1 : 0;
+    pa.prev_luma = h->luma[par ^ 1]; pa.cur_luma = h->luma[par];
+    pa.luma_cam_stride = (int32_t)h->luma_cam_stride;
+    pa.hist = h->strip_hist[par]; pa.n = h->strip_n[par]; pa.sum = h->strip_sum[par]; pa.sumsq = h->strip_sumsq[par];
+    RT_CUDA(h, launch_pass_a(g, pa, 128, h->s_stats));
+    if (prof) RT_CUDA(h, cudaEventRecord(pe.a1, h->s_stats));
+
+    SolveArgs sa{};
+    sa.n = h->strip_n[par]; sa.sum = h->strip_sum[par]; sa.sumsq = h->strip_sumsq[par];
+    sa.maps_new = h->maps_new; sa.E = h->E; sa.q16 = h->q16[qs];
+    sa.K = K; sa.B = p.num_blocks; sa.S = p.strip_width; sa.fit_mode = p.fit_mode; sa.min_valid = p.min_valid;
+    sa.first = first ? 1 : 0; sa.alpha = p.alpha; sa.lambda = p.lambda; sa.gmin = p.gain_min; sa.gmax = p.gain_max;
+    sa.n_groups = h->n_groups; sa.group_start = h->group_start; sa.group_members = h->group_members;
+    sa.left_nbr = h->left_nbr; sa.right_nbr = h->right_nbr; sa.cam_H = h->cam_H;
+    const size_t nb = (size_t)K * 2 * p.num_blocks;
+    // the other slot is what pass A of the next frame set accumulates into
+    sa.clear_u32 = h->strip_hist[par ^ 1]; sa.clear_u32_n = nb * 768 + nb * 3;
+    sa.clear_u64 = h->strip_sum[par ^ 1]; sa.clear_u64_n = nb * 3 * 2;
+    sa.clear2_u32 = nullptr; sa.clear2_u32_n = 0;
+    RT_CUDA(h, launch_solve(sa, h->s_stats));
+    if (prof) RT_CUDA(h, cudaEventRecord(pe.s1, h->s_stats));
+    RT_CUDA(h, cudaEventRecord(h->ev_solved[ev], h->s_stats));
+
+    // main chain: clear frame histograms -> pass B -> crops
+    const int32_t *q_apply = h->q16[qs];
+    if (p.schedule == RT_SCHED_CURRENT) {
+        RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_solved[ev], 0));
+    } else {
+        if (first) {
+            q_apply = h->q16_identity;
+        } else {
+            const int evp = (int)((t + kEvRing - 1) % kEvRing);
+            RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_solved[evp], 0));
+            q_apply = h->q16[(int)((t + kQRing - 1) % kQRing)];
+        }
+    }
+    uint32_t *fh = (p.flags & RT_FLAG_FRAME_STATS) ? h->frame_hist[par] : nullptr;
+    if (fh) RT_CUDA(h, cudaMemsetAsync(fh, 0, (size_t)K * 768 * 4, h->s_main));
+    PassBArgs pb{};
+    pb.q16 = q_apply; pb.frame_hist = fh; pb.thumbs = nullptr;
+    if (prof) RT_CUDA(h, cudaEventRecord(pe.b0, h->s_main));
+    RT_CUDA(h, launch_pass_b(g, pb, h->pb_grid, h->pb_threads, h->pb_smem, h->s_main));
+    if (prof) RT_CUDA(h, cudaEventRecord(pe.b1, h->s_main));
+    if (n_crops > 0) {
+        const rt_crop *table = crop_table;
+        if (!table) {
+            rt_crop *slot = h->crop_host + (size_t)par * p.max_crops;
+            // the pinned slot was last read by the copy of frame set t-2
+            if (t >= 2 && h->launched[ev2]) {
+                rt_status s = wait_event(h, h->ev_done[ev2], -1);
+                if (s != RT_OK) return s;
+            }
+            memcpy(slot, crops, sizeof(rt_crop) * n_crops);
+            RT_CUDA(h, cudaMemcpyAsync(h->crop_dev[par], slot, sizeof(rt_crop) * n_crops, cudaMemcpyHostToDevice,
+                                       h->s_main));
+            table = h->crop_dev[par];
+        }
+        CropArgs ca{};
+        ca.crops = table; ca.n = n_crops; ca.S = p.crop_size; ca.out = h->crops[par];
+        RT_CUDA(h, launch_crops(g, ca, h->s_main));
+        if (prof) RT_CUDA(h, cudaEventRecord(pe.c1, h->s_main));
+    }
+    if (prof) {
+        pe.crops = n_crops > 0;
+        (h->capturing ? h->cap_prof : h->prof).push_back(pe);
+    }
+    h->n_crops[par] = n_crops;
+    RT_CUDA(h, cudaEventRecord(h->ev_done[ev], h->s_main));
+    h->launched[ev] = true;
+    h->out_launched[ev] = false;
+    h->last_first = first;
+    h->restart = false;
+    h->last_was_graph = false;
+    h->t = t + 1;
+    return RT_OK;
+}
+
+rt_status check_planes(rt_handle *h, const void *const *y_planes, const void *const *uv_planes)
+{
+    if (!y_planes) return fail(h, RT_ERR_INVALID, "y_planes is NULL");
+    for (int k = 0; k < h->p.num_cameras; ++k) {
+        const void *yp = y_planes[k];
+        if (!yp || ((uintptr_t)yp & 15)) return fail(h, RT_ERR_INVALID, "a Y / mono plane is NULL or not 16-byte aligned");
+        if (h->cams[k].format == RT_NV12) {
+            const void *uvp = uv_planes ? uv_planes[k] : nullptr;
+            if (!uvp || ((uintptr_t)uvp & 15)) return fail(h, RT_ERR_INVALID, "a UV plane is NULL or not 16-byte aligned");
+        }
+    }
+    return RT_OK;
+}
+
+int last_ev(const rt_handle *h) { return (int)((h->t - 1) % kEvRing); }
+
+}  // namespace
+
+extern "C" {
+
+void rt_default_params(rt_array_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->topology = RT_LINEAR;
+    p->strip_width = 32;
+    p->num_blocks = 1;
+    p->fit_mode = RT_FIT_GLOBAL;
+    p->schedule = RT_SCHED_CURRENT;
+    p->motion_threshold = 24;
+    p->min_valid = 64;
+    p->color_matrix = RT_BT709;
+    p->alpha = 0.05;
+    p->lambda = 1e-6;
+    p->gain_min = 0.25;
+    p->gain_max = 4.0;
+    p->flags = RT_FLAG_FRAME_STATS;
+}
+
+rt_status rt_array_config(const rt_array_params *params, void *cuda_stream, rt_handle **out)
+{
+    if (!out) return fail(nullptr, RT_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    rt_status s = validate(params);
+    if (s != RT_OK) return s;
+    rt_handle *h = new rt_handle();
+    h->p = *params;
+    h->cams.assign(params->cams, params->cams + params->num_cameras);
+    h->p.cams = nullptr;
+    h->user = static_cast<cudaStream_t>(cuda_stream);
+    s = setup(h);
+    if (s != RT_OK) {
+        g_config_error = h->err;
+        free_all(h);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return RT_OK;
+}
+
+rt_status rt_submit_frames(rt_handle *h, const void *const *y_planes, const void *const *uv_planes,
+                           int64_t frame_index, const rt_crop *crops, int32_t n_crops)
+{
+    if (!h) return RT_ERR_INVALID;
+    rt_status s = check_planes(h, y_planes, uv_planes);
+    if (s != RT_OK) return s;
+    s = check_crops(h, crops, n_crops);
+    if (s != RT_OK) return s;
+    return enqueue(h, y_planes, uv_planes, frame_index, crops, n_crops, false);
+}
+
+rt_status rt_submit_frames_host(rt_handle *h, const void *const *y_planes, const void *const *uv_planes,
+                                int64_t frame_index, const rt_crop *crops, int32_t n_crops,
+                                void *const *rgb_out, int64_t rgb_out_pitch)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (!y_planes) return fail(h, RT_ERR_INVALID, "y_planes is NULL");
+    const int K = h->p.num_cameras;
+    rt_status s = check_crops(h, crops, n_crops);
+    if (s != RT_OK) return s;
+    if (!h->stage[0]) {
+        size_t off = 0;
+        h->stage_y_off.resize(K);
+        h->stage_uv_off.resize(K);
+        for (int k = 0; k < K; ++k) {
+            const rt_camera_desc &c = h->cams[k];
+            h->stage_y_off[k] = off;
+            off += align_up((size_t)c.y_pitch * c.height, 256);
+            h->stage_uv_off[k] = off;
+            if (c.format == RT_NV12) off += align_up((size_t)c.uv_pitch * (c.height / 2), 256);
+        }
+        h->stage_bytes = off;
+        for (int i = 0; i < 2; ++i)
+            if ((s = dalloc(h, &h->stage[i], off)) != RT_OK) return s;
+    }
+    const int par = (int)(h->t & 1);
+    const int ev2 = (int)((h->t + kEvRing - 2) % kEvRing);
+    if (h->t >= 2 && h->launched[ev2]) RT_CUDA(h, cudaStreamWaitEvent(h->s_copy, h->ev_done[ev2], 0));
+    RT_CUDA(h, cudaEventRecord(h->ev_user, h->user));
+    RT_CUDA(h, cudaStreamWaitEvent(h->s_copy, h->ev_user, 0));
+    std::vector<const void *> yd(K), uvd(K);
+    for (int k = 0; k < K; ++k) {
+        const rt_camera_desc &c = h->cams[k];
+        if (!y_planes[k]) return fail(h, RT_ERR_INVALID, "a Y / mono plane is NULL");
+        uint8_t *dy = h->stage[par] + h->stage_y_off[k];
+        RT_CUDA(h, cudaMemcpyAsync(dy, y_planes[k], (size_t)c.y_pitch * c.height, cudaMemcpyHostToDevice, h->s_copy));
+        yd[k] = dy;
+        uvd[k] = nullptr;
+        if (c.format == RT_NV12) {
+            if (!uv_planes || !uv_planes[k]) return fail(h, RT_ERR_INVALID, "a UV plane is NULL");
+            uint8_t *duv = h->stage[par] + h->stage_uv_off[k];
+            RT_CUDA(h, cudaMemcpyAsync(duv, uv_planes[k], (size_t)c.uv_pitch * (c.height / 2), cudaMemcpyHostToDevice,
+                                       h->s_copy));
+            uvd[k] = duv;
+        }
+    }
+    if (rgb_out) {
+        for (int k = 0; k < K; ++k)
+            if (!rgb_out[k] || rgb_out_pitch < 3LL * h->cams[k].width)
+                return fail(h, RT_ERR_INVALID, "rgb_out[k] NULL or rgb_out_pitch < 3*width");
+    }
+    const int64_t t = h->t;
+    s = enqueue(h, yd.data(), uvd.data(), frame_index, crops, n_crops, true);
+    if (s != RT_OK || !rgb_out) return s;
+    // device -> host copy of the corrected images, overlapping the next frame set
+    const int ev = (int)(t % kEvRing), opar = (int)(t & 1);
+    RT_CUDA(h, cudaStreamWaitEvent(h->s_d2h, h->ev_done[ev], 0));
+    for (int k = 0; k < K; ++k)
+        RT_CUDA(h, cudaMemcpy2DAsync(rgb_out[k], (size_t)rgb_out_pitch, h->rgb[opar] + h->rgb_off[k],
+                                     (size_t)h->geom.cam[k].rgb_pitch, (size_t)3 * h->cams[k].width,
+                                     h->cams[k].height, cudaMemcpyDeviceToHost, h->s_d2h));
+    RT_CUDA(h, cudaEventRecord(h->ev_out[ev], h->s_d2h));
+    h->out_launched[ev] = true;
+    return RT_OK;
+}
+
+rt_status rt_get_gains(rt_handle *h, double *maps_fp64, int32_t *maps_q16, size_t cap, int32_t timeout_ms)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (h->t == 0) return fail(h, RT_ERR_STATE, "no frame set submitted");
+    if ((maps_fp64 || maps_q16) && cap < h->n_maps) return fail(h, RT_ERR_INVALID, "cap too small");
+    rt_status s = wait_event(h, h->ev_done[last_ev(h)], timeout_ms);
+    if (s != RT_OK) return s;
+    const int64_t t = h->t - 1;
+    const int32_t *q = h->q16[(int)(t % kQRing)];
+    if (h->p.schedule == RT_SCHED_LAGGED) {
+        // the table applied to frame set t came from frame set t-1 (identity when t restarted)
+        q = h->last_first ? h->q16_identity : h->q16[(int)((t + kQRing - 1) % kQRing)];
+    }
+    if (maps_fp64) RT_CUDA(h, cudaMemcpy(maps_fp64, h->E, h->n_maps * 8, cudaMemcpyDeviceToHost));
+    if (maps_q16) RT_CUDA(h, cudaMemcpy(maps_q16, q, h->n_maps * 4, cudaMemcpyDeviceToHost));
+    return RT_OK;
+}
+
+rt_status rt_get_corrected(rt_handle *h, int32_t cam, const uint8_t **dev_rgb, int32_t *pitch, int32_t timeout_ms)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (cam < 0 || cam >= h->p.num_cameras || !dev_rgb || !pitch) return fail(h, RT_ERR_INVALID, "bad argument");
+    if (h->t == 0) return fail(h, RT_ERR_STATE, "no frame set submitted");
+    rt_status s = wait_event(h, h->ev_done[last_ev(h)], timeout_ms);
+    if (s != RT_OK) return s;
+    *dev_rgb = h->rgb[(int)((h->t - 1) & 1)] + h->rgb_off[cam];
+    *pitch = h->geom.cam[cam].rgb_pitch;
+    return RT_OK;
+}
+
+rt_status rt_copy_corrected(rt_handle *h, int32_t cam, void *dst, int64_t dst_pitch, int32_t timeout_ms)
+{
+    const uint8_t *src = nullptr;
+    int32_t pitch = 0;
+    rt_status s = rt_get_corrected(h, cam, &src, &pitch, timeout_ms);
+    if (s != RT_OK) return s;
+    const rt_camera_desc &c = h->cams[cam];
+    if (!dst || dst_pitch < 3LL * c.width) return fail(h, RT_ERR_INVALID, "dst NULL or dst_pitch < 3*width");
+    RT_CUDA(h, cudaMemcpy2DAsync(dst, (size_t)dst_pitch, src, (size_t)pitch, (size_t)3 * c.width, c.height,
+                                 cudaMemcpyDefault, h->s_d2h));
+    RT_CUDA(h, cudaEventRecord(h->ev_tmp, h->s_d2h));
+    return wait_event(h, h->ev_tmp, timeout_ms);
+}
+
+rt_status rt_get_crops(rt_handle *h, const void **dev_fp16_nchw, int32_t *n, int32_t timeout_ms)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (!dev_fp16_nchw || !n) return fail(h, RT_ERR_INVALID, "bad argument");
+    if (h->t == 0) return fail(h, RT_ERR_STATE, "no frame set submitted");
+    rt_status s = wait_event(h, h->ev_done[last_ev(h)], timeout_ms);
+    if (s != RT_OK) return s;
+    const int par = (int)((h->t - 1) & 1);
+    *dev_fp16_nchw = h->crops[par];
+    *n = h->n_crops[par];
+    return RT_OK;
+}
+
+rt_status rt_get_stats(rt_handle *h, rt_stats_view *out, int32_t timeout_ms)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (!out) return fail(h, RT_ERR_INVALID, "out is NULL");
+    if (h->t == 0) return fail(h, RT_ERR_STATE, "no frame set submitted");
+    rt_status s = wait_event(h, h->ev_done[last_ev(h)], timeout_ms);
+    if (s != RT_OK) return s;
+    const int par = (int)((h->t - 1) & 1);
+    out->strip_hist = h->strip_hist[par];
+    out->strip_n = h->strip_n[par];
+    out->strip_sum = reinterpret_cast<const uint64_t *>(h->strip_sum[par]);
+    out->strip_sumsq = reinterpret_cast<const uint64_t *>(h->strip_sumsq[par]);
+    out->frame_hist = (h->p.flags & RT_FLAG_FRAME_STATS) ? h->frame_hist[par] : nullptr;
+    out->thumbs = nullptr;
+    out->num_cameras = h->p.num_cameras;
+    out->num_blocks = h->p.num_blocks;
+    return RT_OK;
+}
+
+rt_status rt_copy_out(rt_handle *h, void *dst, const void *src, size_t bytes, int32_t timeout_ms)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (!dst || !src) return fail(h, RT_ERR_INVALID, "dst or src is NULL");
+    if (h->t > 0) {
+        rt_status s = wait_event(h, h->ev_done[last_ev(h)], timeout_ms);
+        if (s != RT_OK) return s;
+    }
+    RT_CUDA(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->s_d2h));
+    RT_CUDA(h, cudaEventRecord(h->ev_tmp, h->s_d2h));
+    return wait_event(h, h->ev_tmp, timeout_ms);
+}
+
+rt_status rt_stream_wait(rt_handle *h, void *cuda_stream)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (h->t == 0) return RT_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int ev = last_ev(h);
+    RT_CUDA(h, cudaStreamWaitEvent(st, h->ev_done[ev], 0));
+    if (h->out_launched[ev]) RT_CUDA(h, cudaStreamWaitEvent(st, h->ev_out[ev], 0));
+    return RT_OK;
+}
+
+rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y_planes,
+                              const void *const *uv_planes, const rt_crop *crops, const int32_t *n_crops)
+{
+    if (!h) return RT_ERR_INVALID;
+    const int K = h->p.num_cameras, M = h->p.max_crops;
+    if (n_sets <= 0 || n_sets % 6) return fail(h, RT_ERR_INVALID, "n_sets must be a positive multiple of 6");
+    if (h->t == 0) return fail(h, RT_ERR_STATE, "submit the first frame set of the sequence before capturing");
+    if (!y_planes) return fail(h, RT_ERR_INVALID, "y_planes is NULL");
+    rt_status s;
+    for (int i = 0; i < n_sets; ++i) {
+        if ((s = check_planes(h, y_planes + (size_t)i * K, uv_planes ? uv_planes + (size_t)i * K : nullptr)) != RT_OK)
+            return s;
+        const int nc = n_crops ? n_crops[i] : 0;
+        if ((s = check_crops(h, crops ? crops + (size_t)i * M : nullptr, nc)) != RT_OK) return s;
+    }
+    if ((s = rt_sync(h, -1)) != RT_OK) return s;
+    if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    // crop windows of every ring slot, uploaded once
+    if (M > 0 && crops) {
+        const size_t need = (size_t)n_sets * M;
+        if (h->cap_crops_n < need) {
+            if (h->cap_crops) cudaFree(h->cap_crops);
+            h->cap_crops = nullptr;
+            h->cap_crops_n = 0;
+            if ((s = dalloc(h, &h->cap_crops, need)) != RT_OK) return s;
+            h->cap_crops_n = need;
+        }
+        RT_CUDA(h, cudaMemcpy(h->cap_crops, crops, need * sizeof(rt_crop), cudaMemcpyHostToDevice));
+    }
+    // sequencing state to restore: capturing enqueues nothing that runs
+    const int64_t t0 = h->t;
+    bool launched[kEvRing], out_launched[kEvRing];
+    memcpy(launched, h->launched, sizeof launched);
+    memcpy(out_launched, h->out_launched, sizeof out_launched);
+    const bool last_first = h->last_first, restart = h->restart;
+    h->cap_prof.clear();
+    h->graph_launched = false;
+    h->capturing = true;
+    h->cap_t0 = t0;
+    RT_CUDA(h, cudaStreamBeginCapture(h->s_main, cudaStreamCaptureModeThreadLocal));
+    rt_status st = RT_OK;
+    cudaError_t e = cudaEventRecord(h->ev_fork, h->s_main);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_stats, h->ev_fork, 0);
+    if (e != cudaSuccess) st = cuda_fail(h, e, "fork");
+    for (int i = 0; i < n_sets && st == RT_OK; ++i) {
+        const int nc = n_crops ? n_crops[i] : 0;
+        st = enqueue(h, y_planes + (size_t)i * K, uv_planes ? uv_planes + (size_t)i * K : nullptr, 1,
+                     crops ? crops + (size_t)i * M : nullptr, nc, false,
+                     nc > 0 ? h->cap_crops + (size_t)i * M : nullptr);
+    }
+    if (st == RT_OK) {
+        e = cudaEventRecord(h->ev_join, h->s_stats);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_main, h->ev_join, 0);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "join");
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->s_main, &graph);
+    h->capturing = false;
+    h->t = t0;
+    memcpy(h->launched, launched, sizeof launched);
+    memcpy(h->out_launched, out_launched, sizeof out_launched);
+    h->last_first = last_first;
+    h->restart = restart;
+    if (st != RT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    h->graph = graph;
+    RT_CUDA(h, cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
+    RT_CUDA(h, cudaGraphUpload(h->graph_exec, h->s_main));
+    h->cap_n = n_sets;
+    return RT_OK;
+}
+
+rt_status rt_launch_sequence(rt_handle *h)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (!h->graph_exec) return fail(h, RT_ERR_STATE, "no captured sequence");
+    if ((h->t - h->cap_t0) % 6 != 0) return fail(h, RT_ERR_STATE, "frame sets submitted since the capture broke its slot alignment");
+    RT_CUDA(h, cudaEventRecord(h->ev_user, h->user));
+    RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_user, 0));
+    // earlier frame sets' statistics chain and copies finish before the graph starts
+    RT_CUDA(h, cudaEventRecord(h->ev_tmp, h->s_stats));
+    RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_tmp, 0));
+    RT_CUDA(h, cudaEventRecord(h->ev_tmp, h->s_d2h));
+    RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_tmp, 0));
+    RT_CUDA(h, cudaGraphLaunch(h->graph_exec, h->s_main));
+    h->t += h->cap_n;
+    const int ev = last_ev(h);
+    RT_CUDA(h, cudaEventRecord(h->ev_done[ev], h->s_main));
+    // the graph ran everything up to its last frame set on the main stream
+    for (int i = 0; i < kEvRing; ++i) {
+        if (i != ev) RT_CUDA(h, cudaEventRecord(h->ev_done[i], h->s_main));
+        h->launched[i] = true;
+        h->out_launched[i] = false;
+    }
+    h->last_first = false;
+    h->restart = false;
+    h->last_was_graph = true;
+    h->graph_launched = true;
+    return RT_OK;
+}
+
+rt_status rt_profile(rt_handle *h, int32_t enable)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (enable) {
+        rt_status s = rt_sync(h, -1);
+        if (s != RT_OK) return s;
+        h->prof.clear();
+        // events captured into a graph keep their pool slots
+        h->ev_pool_used = h->cap_prof.size() * 6;
+        if (h->cap_prof.empty()) h->ev_pool_used = 0;
+    }
+    h->prof_on = enable != 0;
+    return RT_OK;
+}
+
+rt_status rt_get_profile(rt_handle *h, rt_profile_report *out, int32_t timeout_ms)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (!out) return fail(h, RT_ERR_INVALID, "out is NULL");
+    rt_status s = rt_sync(h, timeout_ms);
+    if (s != RT_OK) return s;
+    memset(out, 0, sizeof *out);
+    // a launched graph reports its last launch; otherwise the single submits
+    const std::vector<ProfEv> &v = (h->graph_launched && !h->cap_prof.empty()) ? h->cap_prof : h->prof;
+    for (const ProfEv &pe : v) {
+        float a = 0, b = 0, c = 0, d = 0;
+        RT_CUDA(h, cudaEventElapsedTime(&a, pe.a0, pe.a1));
+        RT_CUDA(h, cudaEventElapsedTime(&b, pe.a1, pe.s1));
+        RT_CUDA(h, cudaEventElapsedTime(&c, pe.b0, pe.b1));
+        if (pe.crops) RT_CUDA(h, cudaEventElapsedTime(&d, pe.b1, pe.c1));
+        out->pass_a_ms += a;
+        out->solve_ms += b;
+        out->pass_b_ms += c;
+        out->crops_ms += d;
+        out->frame_sets += 1;
+    }
+    return RT_OK;
+}
+
+rt_status rt_sync(rt_handle *h, int32_t timeout_ms)
+{
+    if (!h) return RT_ERR_INVALID;
+    cudaStream_t ss[] = {h->s_copy, h->s_stats, h->s_main, h->s_d2h};
+    for (auto st : ss) {
+        RT_CUDA(h, cudaEventRecord(h->ev_tmp, st));
+        rt_status s = wait_event(h, h->ev_tmp, timeout_ms);
+        if (s != RT_OK) return s;
+    }
+    return RT_OK;
+}
+
+rt_status rt_save_state(rt_handle *h, void *buf, size_t *len)
+{
+    if (!h || !len) return RT_ERR_INVALID;
+    const size_t luma_bytes = (size_t)h->p.num_cameras * h->luma_cam_stride;
+    const size_t need = 4 * sizeof(uint32_t) + sizeof(int64_t) + h->n_maps * 8 + luma_bytes;
+    if (!buf) { *len = need; return RT_OK; }
+    if (*len < need) { *len = need; return fail(h, RT_ERR_INVALID, "buffer too small"); }
+    rt_status s = rt_sync(h, -1);
+    if (s != RT_OK) return s;
+    uint8_t *b = static_cast<uint8_t *>(buf);
+    uint32_t hdr[4] = {kStateMagic, (uint32_t)h->n_maps, (uint32_t)luma_bytes, h->restart ? 1u : 0u};
+    memcpy(b, hdr, sizeof hdr);
+    b += sizeof hdr;
+    int64_t t = h->t;
+    memcpy(b, &t, sizeof t);
+    b += sizeof t;
+    RT_CUDA(h, cudaMemcpy(b, h->E, h->n_maps * 8, cudaMemcpyDeviceToHost));
+    b += h->n_maps * 8;
+    if (h->t > 0) RT_CUDA(h, cudaMemcpy(b, h->luma[(int)((h->t - 1) & 1)], luma_bytes, cudaMemcpyDeviceToHost));
+    else memset(b, 0, luma_bytes);
+    *len = need;
+    return RT_OK;
+}
+
+rt_status rt_load_state(rt_handle *h, const void *buf, size_t len)
+{
+    if (!h || !buf) return RT_ERR_INVALID;
+    const size_t luma_bytes = (size_t)h->p.num_cameras * h->luma_cam_stride;
+    const size_t need = 4 * sizeof(uint32_t) + sizeof(int64_t) + h->n_maps * 8 + luma_bytes;
+    if (len != need) return fail(h, RT_ERR_INVALID, "state blob of another configuration");
+    const uint8_t *b = static_cast<const uint8_t *>(buf);
+    uint32_t hdr[4];
+    memcpy(hdr, b, sizeof hdr);
+    if (hdr[0] != kStateMagic || hdr[1] != h->n_maps || hdr[2] != luma_bytes)
+        return fail(h, RT_ERR_INVALID, "state blob of another configuration");
+    rt_status s = rt_sync(h, -1);
+    if (s != RT_OK) return s;
+    b += sizeof hdr;
+    int64_t t;
+    memcpy(&t, b, sizeof t);
+    b += sizeof t;
+    RT_CUDA(h, cudaMemcpy(h->E, b, h->n_maps * 8, cudaMemcpyHostToDevice));
+    b += h->n_maps * 8;
+    // the next frame set compares its band luma with the saved one
+    const int par_prev = (int)((h->t + 1) & 1);
+    RT_CUDA(h, cudaMemcpy(h->luma[par_prev], b, luma_bytes, cudaMemcpyHostToDevice));
+    h->restart = hdr[3] != 0;
+    (void)t;
+    return RT_OK;
+}
+
+const char *rt_last_error(rt_handle *h)
+{
+    return h ? h->err.c_str() : g_config_error.c_str();
+}
+
+void rt_destroy(rt_handle *h)
+{
+    if (!h) return;
+    rt_sync(h, 10000);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal types shared by the kernels and the host runtime of librt.so.
+// Everything a kernel needs per frame set travels by value in its parameter
+// block (constant bank): camera geometry, this frame set's plane addresses,
+// output addresses.  No per-frame host->device table copy is needed.
+#pragma once
+#include <cstdint>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "../../include/rt.h"
+
+namespace rt {
+
+constexpr int kUnitCols = 16;          // columns a thread converts per row
+constexpr int kHistLanes = 32;         // lane-private copies of each histogram bin
+
+struct CamGeom {
+    const uint8_t *y;       // Y plane (NV12) or 16-bit mono plane, this frame set
+    const uint8_t *uv;      // interleaved UV plane (NV12)
+    uint8_t *rgb;           // corrected RGB24 output
+    int32_t W, H, y_pitch, uv_pitch, rgb_pitch;
+    int32_t fmt, shift;     // shift = bit_depth - 8 for mono
+    uint32_t upr;           // units per row pair = ceil(W / 16)
+    uint32_t unit_base;     // first unit of this camera in the array's unit space
+    const int32_t *ramp;    // Q16 ramp weight per column (seam maps)
+};
+
+struct ArrayGeom {
+    CamGeom cam[RT_MAX_CAMERAS];
+    int32_t K, B, fit_mode, matrix;
+    uint32_t units_total;   // sum over cameras of (H/2) * upr
+};
+
+// Pass B: conversion + whole-frame statistics + Q16 application.
+struct PassBArgs {
+    const int32_t *q16;       // [K][2][B][3][2]
+    uint32_t *frame_hist;     // [K][3][256] (nullptr: statistics off)
+    uint32_t *thumbs;         // [K][3][36][64] (nullptr: off)
+};
+
+// Pass A work item: one camera side, rows [row0, row1) all inside block j.
+struct StripItem { int16_t cam, side, block, pad; int32_t row0, row1; };
+
+struct PassAArgs {
+    const StripItem *items;
+    int32_t n_items, S, T, first;
+    const uint8_t *prev_luma;   // [K][2][H][S] of the previous frame set
+    uint8_t *cur_luma;          // [K][2][H][S] written for the next one
+    int32_t luma_cam_stride;    // bytes per camera in the luma buffers (2 * Hmax * S)
+    uint32_t *hist;             // [K][2][B][3][256]
+    uint32_t *n;                // [K][2][B][3]
+    unsigned long long *sum, *sumsq;
+};
+
+// Solve: fit + smoothing + quantisation.
+struct SolveArgs {
+    const uint32_t *n;
+    const unsigned long long *sum, *sumsq;
+    double *maps_new;          // [K][2][B][3][2] this frame set's estimate
+    double *E;                 // [K][2][B][3][2] smoothed estimate (state)
+    int32_t *q16;              // [K][2][B][3][2]
+    int32_t K, B, S, fit_mode, min_valid, first;
+    double alpha, lambda, gmin, gmax;
+    // seam chains
+    int32_t n_groups;
+    const int32_t *group_start;   // [n_groups + 1] offsets into group_members
+    const int32_t *group_members; // cameras of each chain, by position
+    const int32_t *left_nbr;      // [K] camera whose right band meets my left band, -1 none
+    const int32_t *right_nbr;     // [K]
+    const int32_t *cam_H;         // [K]
+    // buffers to clear for the next frame set (may be null)
+    uint32_t *clear_u32; size_t clear_u32_n;
+    unsigned long long *clear_u64; size_t clear_u64_n;
+    uint32_t *clear2_u32; size_t clear2_u32_n;
+};
+
+struct CropArgs {
+    const rt_crop *crops;     // device copy of this frame set's windows
+    int32_t n, S;
+    __half *out;              // [n][3][S][S]
+};
+
+// Launchers (each returns the launch's cudaError_t).
+cudaError_t launch_pass_b(const ArrayGeom &g, const PassBArgs &a, int grid, int threads,
+                          size_t smem, cudaStream_t s);
+cudaError_t pass_b_prepare(int threads, size_t *smem_bytes);
+cudaError_t launch_pass_a(const ArrayGeom &g, const PassAArgs &a, int threads, cudaStream_t s);
+cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s);
+cudaError_t launch_crops(const ArrayGeom &g, const CropArgs &a, cudaStream_t s);
+
+}  // namespace rt

@@ -1,0 +1,310 @@
+"""Thin ctypes binding of librt.so (include/rt.h): argument marshalling only.
+
+Every step of the correction runs in the library's CUDA kernels; torch only
+provides device buffers (tensor data pointers) and the caller's stream.
+Loading fails loudly when librt.so is missing -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librt.so")
+
+RT_OK, RT_ERR_INVALID, RT_ERR_CUDA, RT_ERR_OOM, RT_ERR_NOT_READY, RT_ERR_TIMEOUT, RT_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+RT_NV12, RT_MONO16 = 0, 1
+RT_LINEAR, RT_RING = 0, 1
+RT_FIT_GLOBAL, RT_FIT_SEAM_AFFINE = 0, 1
+RT_SCHED_CURRENT, RT_SCHED_LAGGED = 0, 1
+RT_BT709, RT_BT601 = 0, 1
+RT_FLAG_FRAME_STATS = 1
+RT_MAX_CAMERAS = 32
+
+# every symbol include/rt.h declares (checked by the tests)
+EXPORTS = ["rt_default_params", "rt_array_config", "rt_submit_frames", "rt_submit_frames_host",
+           "rt_get_gains", "rt_get_corrected", "rt_copy_corrected", "rt_get_crops", "rt_get_stats",
+           "rt_copy_out", "rt_sync", "rt_save_state", "rt_load_state", "rt_last_error", "rt_destroy",
+           "rt_stream_wait", "rt_capture_sequence", "rt_launch_sequence", "rt_profile", "rt_get_profile"]
+
+c_i32, c_i64, c_dbl, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+
+
+class CameraDesc(ctypes.Structure):
+    _fields_ = [("width", c_i32), ("height", c_i32), ("format", c_i32), ("bit_depth", c_i32),
+                ("y_pitch", c_i32), ("uv_pitch", c_i32), ("group", c_i32), ("position", c_i32)]
+
+
+class ArrayParams(ctypes.Structure):
+    _fields_ = [("num_cameras", c_i32), ("cams", ctypes.POINTER(CameraDesc)), ("topology", c_i32),
+                ("strip_width", c_i32), ("num_blocks", c_i32), ("fit_mode", c_i32), ("schedule", c_i32),
+                ("motion_threshold", c_i32), ("min_valid", c_i32), ("color_matrix", c_i32),
+                ("alpha", c_dbl), ("lambda_", c_dbl), ("gain_min", c_dbl), ("gain_max", c_dbl),
+                ("max_crops", c_i32), ("crop_size", c_i32), ("flags", c_i32)]
+
+
+class Crop(ctypes.Structure):
+    _fields_ = [("cam", c_i32), ("x0", c_i32), ("y0", c_i32), ("w", c_i32), ("h", c_i32)]
+
+
+class ProfileReport(ctypes.Structure):
+    _fields_ = [("frame_sets", c_i32), ("pass_a_ms", c_dbl), ("solve_ms", c_dbl), ("pass_b_ms", c_dbl),
+                ("crops_ms", c_dbl)]
+
+
+class StatsView(ctypes.Structure):
+    _fields_ = [("strip_hist", c_vp), ("strip_n", c_vp), ("strip_sum", c_vp), ("strip_sumsq", c_vp),
+                ("frame_hist", c_vp), ("thumbs", c_vp), ("num_cameras", c_i32), ("num_blocks", c_i32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load librt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("librt.so not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    L.rt_default_params.argtypes = [ctypes.POINTER(ArrayParams)]
+    L.rt_default_params.restype = None
+    L.rt_array_config.argtypes = [ctypes.POINTER(ArrayParams), c_vp, ctypes.POINTER(c_vp)]
+    L.rt_submit_frames.argtypes = [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_i64, ctypes.POINTER(Crop), c_i32]
+    L.rt_submit_frames_host.argtypes = [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_i64,
+                                        ctypes.POINTER(Crop), c_i32, ctypes.POINTER(c_vp), c_i64]
+    L.rt_get_gains.argtypes = [c_vp, c_vp, c_vp, c_sz, c_i32]
+    L.rt_get_corrected.argtypes = [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_i32), c_i32]
+    L.rt_copy_corrected.argtypes = [c_vp, c_i32, c_vp, c_i64, c_i32]
+    L.rt_get_crops.argtypes = [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_i32), c_i32]
+    L.rt_get_stats.argtypes = [c_vp, ctypes.POINTER(StatsView), c_i32]
+    L.rt_copy_out.argtypes = [c_vp, c_vp, c_vp, c_sz, c_i32]
+    L.rt_sync.argtypes = [c_vp, c_i32]
+    L.rt_save_state.argtypes = [c_vp, c_vp, ctypes.POINTER(c_sz)]
+    L.rt_load_state.argtypes = [c_vp, c_vp, c_sz]
+    L.rt_last_error.argtypes = [c_vp]
+    L.rt_last_error.restype = ctypes.c_char_p
+    L.rt_stream_wait.argtypes = [c_vp, c_vp]
+    L.rt_capture_sequence.argtypes = [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp),
+                                      ctypes.POINTER(Crop), ctypes.POINTER(c_i32)]
+    L.rt_launch_sequence.argtypes = [c_vp]
+    L.rt_profile.argtypes = [c_vp, c_i32]
+    L.rt_get_profile.argtypes = [c_vp, ctypes.POINTER(ProfileReport), c_i32]
+    L.rt_destroy.argtypes = [c_vp]
+    L.rt_destroy.restype = None
+    for name in EXPORTS:
+        fn = getattr(L, name)
+        if fn.restype is ctypes.c_int:   # default restype: rt_status
+            fn.restype = c_i32
+    _lib = L
+    return L
+
+
+class RtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("rt status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _check(L, h, st):
+    if st != RT_OK:
+        msg = L.rt_last_error(h)
+        raise RtError(st, msg.decode() if msg else "")
+
+
+def default_params() -> ArrayParams:
+    p = ArrayParams()
+    load().rt_default_params(ctypes.byref(p))
+    return p
+
+
+def camera_desc(cam) -> CameraDesc:
+    """From any object with width/height/fmt/bit_depth/y_pitch/uv_pitch/group/position."""
+    return CameraDesc(cam.width, cam.height, cam.fmt, getattr(cam, "bit_depth", 8), cam.y_pitch,
+                      getattr(cam, "uv_pitch", 0), getattr(cam, "group", 0), getattr(cam, "position", 0))
+
+
+class CameraArray:
+    """One configured camera array (a handle of librt.so)."""
+
+    def __init__(self, cams, stream=None, **kw):
+        import torch
+        self.L = load()
+        self.cams = list(cams)
+        self.K = len(self.cams)
+        p = default_params()
+        self._descs = (CameraDesc * self.K)(*[camera_desc(c) for c in self.cams])
+        p.num_cameras = self.K
+        p.cams = ctypes.cast(self._descs, ctypes.POINTER(CameraDesc))
+        for k, v in kw.items():
+            setattr(p, "lambda_" if k == "lam" else k, v)
+        self.p = p
+        self.B = p.num_blocks
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.h = c_vp()
+        st = self.L.rt_array_config(ctypes.byref(p), c_vp(sp), ctypes.byref(self.h))
+        if st != RT_OK:
+            raise RtError(st, self.L.rt_last_error(None).decode())
+        self._keep: List[object] = []
+
+    # -- submission ------------------------------------------------------
+    def _planes(self, frames):
+        y = (c_vp * self.K)()
+        uv = (c_vp * self.K)()
+        for k, f in enumerate(frames):
+            if "ir" in f:
+                y[k] = f["ir"].data_ptr()
+                uv[k] = None
+            else:
+                y[k] = f["y"].data_ptr()
+                uv[k] = f["uv"].data_ptr()
+        return y, uv
+
+    @staticmethod
+    def _crops(crops):
+        n = len(crops)
+        arr = (Crop * max(1, n))(*[Crop(*map(int, c)) for c in crops])
+        return arr, n
+
+    def submit_frames(self, frames: Sequence[Dict[str, object]], frame_index: int, crops=()):
+        y, uv = self._planes(frames)
+        arr, n = self._crops(crops)
+        st = self.L.rt_submit_frames(self.h, y, uv, int(frame_index), arr, n)
+        _check(self.L, self.h, st)
+        self._keep = (self._keep + [frames])[-3:]
+
+    def submit_frames_host(self, frames, frame_index: int, crops=(), rgb_out=None, rgb_out_pitch=0):
+        y, uv = self._planes(frames)
+        arr, n = self._crops(crops)
+        outp = None
+        if rgb_out is not None:
+            outp = (c_vp * self.K)(*[t.data_ptr() for t in rgb_out])
+        st = self.L.rt_submit_frames_host(self.h, y, uv, int(frame_index), arr, n, outp, int(rgb_out_pitch))
+        _check(self.L, self.h, st)
+        self._keep = (self._keep + [(frames, rgb_out)])[-3:]
+
+    # -- results ---------------------------------------------------------
+    def get_gains(self, timeout_ms: int = 60000):
+        shape = (self.K, 2, self.B, 3, 2)
+        maps = np.zeros(shape, np.float64)
+        q = np.zeros(shape, np.int32)
+        st = self.L.rt_get_gains(self.h, maps.ctypes.data, q.ctypes.data, maps.size, timeout_ms)
+        _check(self.L, self.h, st)
+        return maps, q
+
+    def get_corrected(self, cam: int, timeout_ms: int = 60000):
+        """Corrected RGB24 of camera cam as a device tensor [H, W, 3] (a copy)."""
+        import torch
+        c = self.cams[cam]
+        out = torch.empty((c.height, c.width, 3), dtype=torch.uint8, device="cuda")
+        st = self.L.rt_copy_corrected(self.h, cam, out.data_ptr(), 3 * c.width, timeout_ms)
+        _check(self.L, self.h, st)
+        return out
+
+    def copy_out(self, dst_ptr: int, src_ptr: int, nbytes: int, timeout_ms: int = 60000):
+        st = self.L.rt_copy_out(self.h, c_vp(dst_ptr), c_vp(src_ptr), nbytes, timeout_ms)
+        _check(self.L, self.h, st)
+
+    def get_crops(self, timeout_ms: int = 60000):
+        import torch
+        ptr, n = c_vp(), c_i32()
+        st = self.L.rt_get_crops(self.h, ctypes.byref(ptr), ctypes.byref(n), timeout_ms)
+        _check(self.L, self.h, st)
+        S = self.p.crop_size
+        out = torch.empty((n.value, 3, S, S), dtype=torch.float16, device="cuda")
+        if n.value:
+            self.copy_out(out.data_ptr(), ptr.value, out.numel() * 2, timeout_ms)
+        return out
+
+    def get_stats(self, timeout_ms: int = 60000) -> Dict[str, np.ndarray]:
+        v = StatsView()
+        st = self.L.rt_get_stats(self.h, ctypes.byref(v), timeout_ms)
+        _check(self.L, self.h, st)
+        K, B = self.K, self.B
+        out = {}
+        for name, ptr, shape, dt in (("strip_hist", v.strip_hist, (K, 2, B, 3, 256), np.uint32),
+                                     ("strip_n", v.strip_n, (K, 2, B, 3), np.uint32),
+                                     ("strip_sum", v.strip_sum, (K, 2, B, 3), np.uint64),
+                                     ("strip_sumsq", v.strip_sumsq, (K, 2, B, 3), np.uint64),
+                                     ("frame_hist", v.frame_hist, (K, 3, 256), np.uint32)):
+            if not ptr:
+                out[name] = None
+                continue
+            a = np.zeros(shape, dt)
+            self.copy_out(a.ctypes.data, ptr, a.nbytes, timeout_ms)
+            out[name] = a
+        return out
+
+    def stream_wait(self, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _check(self.L, self.h, self.L.rt_stream_wait(self.h, c_vp(sp)))
+
+    def capture_sequence(self, frame_sets, crops_per_set=None):
+        """Capture a graph over a fixed ring of frame sets (len a multiple of 6)."""
+        n = len(frame_sets)
+        y = (c_vp * (n * self.K))()
+        uv = (c_vp * (n * self.K))()
+        for i, fs in enumerate(frame_sets):
+            yi, uvi = self._planes(fs)
+            for k in range(self.K):
+                y[i * self.K + k] = yi[k]
+                uv[i * self.K + k] = uvi[k]
+        cr_p, nc_p = None, None
+        if crops_per_set is not None:
+            M = max(1, self.p.max_crops)
+            flat = []
+            counts = []
+            for cl in crops_per_set:
+                counts.append(len(cl))
+                flat += [Crop(*map(int, c)) for c in cl] + [Crop()] * (M - len(cl))
+            cr_p = (Crop * len(flat))(*flat)
+            nc_p = (c_i32 * n)(*counts)
+        st = self.L.rt_capture_sequence(self.h, n, y, uv, cr_p, nc_p)
+        _check(self.L, self.h, st)
+        self._captured = frame_sets
+
+    def launch_sequence(self):
+        _check(self.L, self.h, self.L.rt_launch_sequence(self.h))
+
+    def profile(self, enable: bool):
+        _check(self.L, self.h, self.L.rt_profile(self.h, 1 if enable else 0))
+
+    def get_profile(self, timeout_ms: int = 60000) -> Dict[str, float]:
+        r = ProfileReport()
+        _check(self.L, self.h, self.L.rt_get_profile(self.h, ctypes.byref(r), timeout_ms))
+        return {"frame_sets": r.frame_sets, "pass_a_ms": r.pass_a_ms, "solve_ms": r.solve_ms,
+                "pass_b_ms": r.pass_b_ms, "crops_ms": r.crops_ms}
+
+    def sync(self, timeout_ms: int = 60000):
+        _check(self.L, self.h, self.L.rt_sync(self.h, timeout_ms))
+
+    def save_state(self) -> bytes:
+        n = c_sz(0)
+        _check(self.L, self.h, self.L.rt_save_state(self.h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self.L, self.h, self.L.rt_save_state(self.h, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def load_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(self.L, self.h, self.L.rt_load_state(self.h, buf, len(blob)))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.rt_destroy(self.h)
+            self.h = c_vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

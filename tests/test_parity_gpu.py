@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bars (written here, per output):
+  - band and frame statistics, histograms, the Q16 table and the corrected
+    8-bit images: bit-exact;
+  - the FP64 maps (gains, or affine a and b): |gpu - oracle| <= 1e-6 |oracle|
+    + 1e-9 (the same formulas in FP64; only summation order and libm ulps
+    differ);
+  - FP16 crops: within 1e-3 absolute of the oracle's FP64 resample.
+The Q16 table is compared exactly except where the oracle's 65536*E lies
+within 1e-6 of a rounding tie (there both roundings are correct); the
+oracle then applies the GPU's table so the 8-bit output is still compared
+bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+from conftest import np_frames
+from paper_1910_03517_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    from paper_1910_03517_gb300 import build, rt as rtmod
+    build.build()
+    rtmod.load()
+    return rtmod
+
+
+def _params_for_oracle(orc, **kw):
+    m = dict(kw)
+    if "lam" in m:
+        m["lam"] = m.pop("lam")
+    keep = {k: v for k, v in m.items() if k in orc.Params.__dataclass_fields__}
+    return orc.Params(**keep)
+
+
+def _check_q16(q_gpu, q_orc, E):
+    diff = q_gpu.astype(np.int64) - q_orc.astype(np.int64)
+    if not (diff == 0).all():
+        v = 65536.0 * E
+        near_tie = np.abs(np.abs(v - np.floor(v)) - 0.5) < 1e-6 * np.maximum(1.0, np.abs(v))
+        bad = (diff != 0) & ~(near_tie & (np.abs(diff) <= 1))
+        assert not bad.any(), (np.argwhere(bad)[:5], q_gpu[bad][:5], q_orc[bad][:5])
+
+
+def run_sequence(rt, orc, wl, frames, crops_per_frame=0, crop_size=0, device_inputs=True,
+                 stats=True, check_images=True, **kw):
+    """Submit `frames` frame sets to the GPU and the oracle, compare each."""
+    p = _params_for_oracle(orc, **kw)
+    arr = rt.CameraArray(wl.cams, max_crops=max(crops_per_frame, 0), crop_size=max(crop_size, 0),
+                         flags=rt.RT_FLAG_FRAME_STATS if stats else 0, **kw)
+    o = orc.ArrayOracle(wl.cams, p)
+    K = len(wl.cams)
+    results = []
+    for t in range(frames):
+        fs = synth.frame_set(wl, t, device="cuda")
+        crops = synth.crop_list(wl, t, crops_per_frame) if crops_per_frame else []
+        if device_inputs:
+            arr.submit_frames(fs, t, crops)
+        else:
+            host = [{k: v.cpu().pin_memory() for k, v in f.items()} for f in fs]
+            arr.submit_frames_host(host, t, crops)
+        maps, q16 = arr.get_gains()
+        st = arr.get_stats()
+        r = o.step(np_frames(fs), crops=crops, crop_size=crop_size, q16_override=q16,
+                   want_frame_stats=stats)
+        # statistics: bit-exact
+        assert np.array_equal(st["strip_n"], r["strip_n"]), t
+        assert np.array_equal(st["strip_sum"], r["strip_sum"]), t
+        assert np.array_equal(st["strip_sumsq"], r["strip_sumsq"]), t
+        assert np.array_equal(st["strip_hist"], r["strip_hist"]), t
+        if stats:
+            assert np.array_equal(st["frame_hist"], r["frame_hist"]), t
+        # FP64 maps
+        E = r["E"]
+        assert (np.abs(maps - E) <= 1e-6 * np.abs(E) + 1e-9).all(), (t, np.abs(maps - E).max())
+        _check_q16(q16, r["q16"], r["maps"])
+        if check_images:
+            for k in range(K):
+                got = arr.get_corrected(k).cpu().numpy()
+                ref = r["corrected"][k]
+                if not np.array_equal(got, ref):
+                    bad = np.argwhere(got != ref)
+                    raise AssertionError("frame %d cam %d: %d bytes differ, first %s got %s want %s" % (
+                        t, k, len(bad), bad[:3].tolist(), got[tuple(bad[0])], ref[tuple(bad[0])]))
+        if crops:
+            cr = arr.get_crops().float().cpu().numpy()
+            assert cr.shape == r["crops"].shape
+            assert np.abs(cr - r["crops"]).max() < 1e-3, (t, np.abs(cr - r["crops"]).max())
+        results.append((maps, q16))
+    arr.close()
+    return results
+
+
+# ---------------------------------------------------------------------------
+
+def _all_triples(W=4096):
+    H = W
+    b = np.arange(H // 2)[:, None] * (W // 2) + np.arange(W // 2)[None, :]
+    pair = b // 64
+    y = np.zeros((H, W), np.uint8)
+    base = 4 * (b % 64)
+    y[0::2, 0::2] = base
+    y[0::2, 1::2] = base + 1
+    y[1::2, 0::2] = base + 2
+    y[1::2, 1::2] = base + 3
+    uv = np.zeros((H // 2, W), np.uint8)
+    uv[:, 0::2] = (pair // 256).astype(np.uint8)
+    uv[:, 1::2] = (pair % 256).astype(np.uint8)
+    return y, uv
+
+
+@pytest.mark.parametrize("matrix", [0, 1])
+def test_conversion_every_yuv_triple(rt, orc, matrix):
+    y, uv = _all_triples()
+    cam = synth.Camera(4096, 4096)
+    arr = rt.CameraArray([cam], color_matrix=matrix)
+    fr = [{"y": torch.from_numpy(y).cuda(), "uv": torch.from_numpy(uv).cuda()}]
+    arr.submit_frames(fr, 0)
+    got = arr.get_corrected(0).cpu().numpy()          # one camera: no seam, identity gains
+    maps, q16 = arr.get_gains()
+    assert (q16[..., 0] == 65536).all() and (q16[..., 1] == 0).all()
+    ref, _ = orc.convert(cam, {"y": y, "uv": uv}, matrix)
+    assert np.array_equal(got, ref)
+    st = arr.get_stats()
+    assert np.array_equal(st["frame_hist"][0], orc.frame_stats(ref)["hist"])
+    arr.close()
+
+
+def test_small_pair_global(rt, orc):
+    run_sequence(rt, orc, synth.small_pair(), 8)
+
+
+def test_small_pair_seam_affine_16_blocks(rt, orc):
+    run_sequence(rt, orc, synth.small_pair(), 8, fit_mode=1, num_blocks=16)
+
+
+def test_seam_affine_64_blocks_ring_lagged(rt, orc):
+    wl = synth.small_pair()
+    wl.cams = [synth.Camera(640, 480, position=i) for i in range(3)]
+    wl.moving_object = True
+    run_sequence(rt, orc, wl, 5, fit_mode=1, num_blocks=64, topology=1, schedule=1)
+
+
+def test_global_blocks_lagged_moving_object(rt, orc):
+    wl = synth.small_pair()
+    wl.moving_object = True
+    run_sequence(rt, orc, wl, 6, num_blocks=16, schedule=1)
+
+
+def test_ragged_widths_uneven_groups_and_ir(rt, orc):
+    cams = [
+        synth.Camera(72, 38, group=0, position=0, y_pitch=80, uv_pitch=80),
+        synth.Camera(100, 38, group=0, position=1, y_pitch=112, uv_pitch=112),
+        synth.Camera(66, 40, group=0, position=2, y_pitch=80, uv_pitch=96),
+        synth.Camera(90, 20, fmt=synth.MONO16, bit_depth=12, group=1, position=0, y_pitch=192),
+        synth.Camera(64, 20, fmt=synth.MONO16, bit_depth=10, group=1, position=1),
+        synth.Camera(34, 6, group=2, position=0, y_pitch=48, uv_pitch=48),
+    ]
+    wl = synth.Workload("ragged", cams, frames=4, seed=12, glare_cams=(1,))
+    for kw in ({}, {"fit_mode": 1, "num_blocks": 3}, {"num_blocks": 5, "topology": 1}):
+        run_sequence(rt, orc, wl, 4, strip_width=16, min_valid=8, crops_per_frame=0, **kw)
+
+
+def test_crops_edges_and_sizes(rt, orc):
+    wl = synth.small_pair()
+    wl.n_crops, wl.crop_side, wl.crop_out = 12, (1, 480), 48
+    run_sequence(rt, orc, wl, 3, crops_per_frame=12, crop_size=48)
+    wl.crop_side = (40, 64)
+    run_sequence(rt, orc, wl, 2, crops_per_frame=9, crop_size=97)
+
+
+def test_host_input_path_matches(rt, orc):
+    run_sequence(rt, orc, synth.small_pair(), 3, device_inputs=False, crops_per_frame=4, crop_size=32)
+
+
+def test_host_outputs_pipelined(rt):
+    wl = synth.small_pair()
+    a = rt.CameraArray(wl.cams)
+    b = rt.CameraArray(wl.cams)
+    outs = []
+    for t in range(4):
+        fs = synth.frame_set(wl, t, device="cuda")
+        host = [{k: v.cpu().pin_memory() for k, v in f.items()} for f in fs]
+        o = [torch.empty((c.height, 3 * c.width), dtype=torch.uint8).pin_memory() for c in wl.cams]
+        a.submit_frames_host(host, t, rgb_out=o, rgb_out_pitch=3 * 640)
+        b.submit_frames(fs, t)
+        a.sync()
+        for k in range(2):
+            assert torch.equal(o[k].view(480, 640, 3), b.get_corrected(k).cpu())
+        outs.append(o)
+    a.close()
+    b.close()
+
+
+def test_state_save_and_resume(rt, orc):
+    wl = synth.small_pair()
+    a = rt.CameraArray(wl.cams, fit_mode=1, num_blocks=4)
+    for t in range(3):
+        a.submit_frames(synth.frame_set(wl, t, device="cuda"), t)
+    blob = a.save_state()
+    b = rt.CameraArray(wl.cams, fit_mode=1, num_blocks=4)
+    b.load_state(blob)
+    for t in range(3, 6):
+        fs = synth.frame_set(wl, t, device="cuda")
+        a.submit_frames(fs, t)
+        b.submit_frames(fs, t)
+        ma, qa = a.get_gains()
+        mb, qb = b.get_gains()
+        assert np.array_equal(ma, mb) and np.array_equal(qa, qb)
+        assert torch.equal(a.get_corrected(1), b.get_corrected(1))
+    a.close()
+    b.close()
+
+
+def test_get_times_out_instead_of_hanging(rt):
+    wl = synth.small_pair()
+    s = torch.cuda.Stream()
+    a = rt.CameraArray(wl.cams, stream=s)
+    fs = synth.frame_set(wl, 0, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        torch.cuda._sleep(400_000_000)      # finite busy kernel ahead of the submit on the caller's stream
+    a.submit_frames(fs, 0)
+    with pytest.raises(rt.RtError) as ei:
+        a.get_gains(timeout_ms=1)
+    assert ei.value.status == rt.RT_ERR_TIMEOUT
+    a.get_gains(timeout_ms=60000)
+    a.close()
+
+
+def test_tower12_full_size(rt, orc):
+    """12 x 2048 x 1080 with glare and drifting gains, the benchmark's launch shape."""
+    run_sequence(rt, orc, synth.tower12(frames=3), 3)
+
+
+def test_uneven_array_full_size_with_crops(rt, orc):
+    wl = synth.uneven_array(frames=2)
+    run_sequence(rt, orc, wl, 2, crops_per_frame=8, crop_size=512, num_blocks=16)
