@@ -116,7 +116,7 @@ typedef struct {
 } rt_array_params;
 
 #define RT_FLAG_FRAME_STATS 1   /* whole-frame histograms of every camera (S2 iii) */
-#define RT_FLAG_THUMBNAILS 2    /* 64x36 thumbnail cell sums of every camera      */
+#define RT_FLAG_THUMBNAILS 2    /* 64x36 thumbnail cell sums of every camera (surrogate input) */
 
 /* An attention window: rectangle (x0, y0, w, h) of camera cam, inside it. */
 typedef struct { int32_t cam, x0, y0, w, h; } rt_crop;
@@ -199,6 +199,11 @@ typedef struct {
     int32_t num_cameras, num_blocks;
 } rt_stats_view;
 rt_status rt_get_stats(rt_handle *h, rt_stats_view *out, int32_t timeout_ms);
+
+/* Wait, then write the last frame set's thumbnail features into the DEVICE
+ * buffer x_bf16: BF16 [K][3][36][64], cell mean / 255 - 0.5 (the learned
+ * surrogate's input, rt_surrogate.h).  Needs RT_FLAG_THUMBNAILS. */
+rt_status rt_get_thumb_features(rt_handle *h, void *x_bf16, int32_t timeout_ms);
 
 /* Copy bytes from library memory (an address returned by rt_get_stats,
  * rt_get_crops or rt_get_corrected) to dst, host or device memory; complete

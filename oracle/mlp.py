@@ -7,7 +7,10 @@ log-gains; the labels are the log-gains of the per-camera gain fit (one
 block).  The GPU stores operands in BF16 and accumulates in FP32; this
 oracle computes in float64 and, when ``bf16`` is set, rounds to BF16 at the
 same storage points (the input, the weights as used, the hidden activations
-and their gradients) so that the two differ only by accumulation order.
+and their gradients).  With ``acc32`` the sums whose results are rounded to
+BF16 are accumulated in float32 first, so that a BF16 rounding decision is
+taken in the kernel's precision (FP32 accumulation, BF16 storage); the
+remaining difference to the GPU is the order of the FP32 additions.
 Weight layout: W1 [256, 6912], W2 [256, 256], W3 [3, 256] (out x in).
 """
 from __future__ import annotations
@@ -36,14 +39,25 @@ def thumb_features(sums: np.ndarray, W: int, H: int) -> np.ndarray:
     return (sums.astype(np.float64) / area[None] / 255.0 - 0.5).reshape(-1)
 
 
-def forward(P: Dict[str, np.ndarray], X: np.ndarray, bf16: bool = True):
+def _mm(a, b, acc32):
+    """a @ b, accumulated in float32 when acc32 (operands are BF16 values)."""
+    if acc32:
+        return (np.asarray(a, np.float32) @ np.asarray(b, np.float32)).astype(np.float64)
+    return a @ b
+
+
+def _add(z, bias, acc32):
+    return (z.astype(np.float32) + np.asarray(bias, np.float32)).astype(np.float64) if acc32 else z + bias
+
+
+def forward(P: Dict[str, np.ndarray], X: np.ndarray, bf16: bool = True, acc32: bool = False):
     r = bf16_round if bf16 else (lambda a: np.asarray(a, np.float64))
     x = r(X)
-    z1 = x @ r(P["W1"]).T + P["b1"]
+    z1 = _add(_mm(x, r(P["W1"]).T, acc32), P["b1"], acc32)
     h1 = r(np.maximum(z1, 0.0))
-    z2 = h1 @ r(P["W2"]).T + P["b2"]
+    z2 = _add(_mm(h1, r(P["W2"]).T, acc32), P["b2"], acc32)
     h2 = r(np.maximum(z2, 0.0))
-    y = h2 @ r(P["W3"]).T + P["b3"]
+    y = _add(_mm(h2, r(P["W3"]).T, acc32), P["b3"], acc32)
     return y, {"x": x, "z1": z1, "h1": h1, "z2": z2, "h2": h2, "y": y}
 
 
@@ -51,16 +65,19 @@ def mse(y: np.ndarray, t: np.ndarray) -> float:
     return float(np.mean((y - t) ** 2))
 
 
-def backward(P: Dict[str, np.ndarray], cache, t: np.ndarray, bf16: bool = True):
+def backward(P: Dict[str, np.ndarray], cache, t: np.ndarray, bf16: bool = True, acc32: bool = False):
     """Gradients of mean((y - t)^2) over the batch and the three outputs."""
     r = bf16_round if bf16 else (lambda a: np.asarray(a, np.float64))
     N = t.shape[0]
     dy = 2.0 * (cache["y"] - t) / (N * D_OUT)
+    if acc32:
+        dy = (np.float32(2.0) * (cache["y"].astype(np.float32) - np.asarray(t, np.float32)) /
+              np.float32(N * D_OUT)).astype(np.float64)
     g = {"W3": dy.T @ cache["h2"], "b3": dy.sum(0)}
-    dh2 = r((dy @ r(P["W3"])) * (cache["z2"] > 0))
+    dh2 = r(_mm(dy, r(P["W3"]), acc32) * (cache["z2"] > 0))
     g["W2"] = dh2.T @ cache["h1"]
     g["b2"] = dh2.sum(0)
-    dh1 = r((dh2 @ r(P["W2"])) * (cache["z1"] > 0))
+    dh1 = r(_mm(dh2, r(P["W2"]), acc32) * (cache["z1"] > 0))
     g["W1"] = dh1.T @ cache["x"]
     g["b1"] = dh1.sum(0)
     return g

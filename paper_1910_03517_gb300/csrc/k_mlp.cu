@@ -1,0 +1,476 @@
+// Learned gain surrogate (no counterpart in the paper): a camera's 3x36x64
+// thumbnail -> Linear(6912, 256) -> ReLU -> Linear(256, 256) -> ReLU ->
+// Linear(256, 3) -> the camera's three log-gains.  BF16 operands, FP32
+// accumulation on the tcgen05 tensor cores (tc_gemm.cuh), FP32 master
+// weights and Adam moments.  Trained with the mean squared error against the
+// log-gains of the per-camera gain fit.
+//
+// A training step for a batch of 256 thumbnails (M = 256):
+//   fwd1  H1 = relu(X W1^T + b1)        GEMM 256x256x6912, epilogue writes H1, H1^T
+//   fwd2  H2 = relu(H1 W2^T + b2)       GEMM 256x256x256
+//   head  y = H2 W3^T + b3, loss, dy, dW3, db3, dZ2 = (dy W3) * [H2 > 0]  (CUDA cores)
+//   dW2 = dZ2^T H1                      GEMM 256x256x256  (A = dZ2^T, B = H1^T)
+//   dZ1 = (dZ2 W2) * [H1 > 0]           GEMM 256x256x256  (A = dZ2,  B = W2^T)
+//   dW1 = dZ1^T X                       GEMM 256x6912x256 (A = dZ1^T, B = X^T)
+//   db1, db2 (batch sums), Adam over all parameters, BF16 copies of W1, W2, W2^T, W3.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rt_internal.cuh"
+#include "tc_gemm.cuh"
+#include "../../include/rt_surrogate.h"
+
+using namespace rt;
+
+namespace {
+
+constexpr int D_IN = 3 * RT_THUMB_H * RT_THUMB_W;   // 6912
+constexpr int D_H = 256;
+constexpr int D_OUT = 3;
+constexpr int MAXB = 256;
+constexpr size_t OFF_W1 = 0, OFF_B1 = OFF_W1 + (size_t)D_H * D_IN, OFF_W2 = OFF_B1 + D_H,
+                 OFF_B2 = OFF_W2 + (size_t)D_H * D_H, OFF_W3 = OFF_B2 + D_H, OFF_B3 = OFF_W3 + (size_t)D_OUT * D_H,
+                 N_PARAMS = OFF_B3 + D_OUT;
+constexpr int kBN = 128;
+
+using bf16 = __nv_bfloat16;
+
+// ---------------------------------------------------------------------------
+// GEMM kernels with fused epilogues
+// ---------------------------------------------------------------------------
+
+struct EpiReluBias {            // out = bf16(relu(v + bias[col])), row-major and (optionally) transposed
+    const float *bias;
+    bf16 *out; int ld;          // [M][N]
+    bf16 *outT; int ldT;        // [N][M] or nullptr
+    __device__ void operator()(int row, int col0, const float *v) const
+    {
+        bf16 h[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) h[i] = __float2bfloat16_rn(fmaxf(v[i] + bias[col0 + i], 0.0f));
+        uint4 *d = reinterpret_cast<uint4 *>(out + (size_t)row * ld + col0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d[i] = reinterpret_cast<const uint4 *>(h)[i];
+        if (outT) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) outT[(size_t)(col0 + i) * ldT + row] = h[i];
+        }
+    }
+};
+
+struct EpiMaskT {               // outT[col][row] = bf16(v * [H[row][col] > 0])
+    const bf16 *H; int ldH;
+    bf16 *outT; int ldT;
+    __device__ void operator()(int row, int col0, const float *v) const
+    {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const float hv = __bfloat162float(H[(size_t)row * ldH + col0 + i]);
+            outT[(size_t)(col0 + i) * ldT + row] = __float2bfloat16_rn(hv > 0.0f ? v[i] : 0.0f);
+        }
+    }
+};
+
+struct EpiStore {               // out[row][col] = v (FP32)
+    float *out; int ld;
+    __device__ void operator()(int row, int col0, const float *v) const
+    {
+        float4 *d = reinterpret_cast<float4 *>(out + (size_t)row * ld + col0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    }
+};
+
+template <class Epi>
+__global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB, int K, Epi epi,
+                                                      int *err)
+{
+    tc::gemm_tile<kBN>(&tmA, &tmB, K, epi, err);
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core kernels
+// ---------------------------------------------------------------------------
+
+// Output layer, loss and its backward for one batch row per CTA (256 threads).
+__global__ void __launch_bounds__(256) head_kernel(const bf16 *__restrict__ H2, const float *__restrict__ P,
+                                                   const float *__restrict__ T, int n_valid, float *__restrict__ Y,
+                                                   float *__restrict__ G, bf16 *__restrict__ dZ2,
+                                                   bf16 *__restrict__ dZ2T, float *__restrict__ loss, int Mb,
+                                                   int want_grad)
+{
+    const int b = blockIdx.x, i = threadIdx.x;
+    __shared__ float red[D_OUT][8];
+    __shared__ float dy[D_OUT];
+    const float h = __bfloat162float(H2[(size_t)b * D_H + i]);
+    float w[D_OUT];
+#pragma unroll
+    for (int o = 0; o < D_OUT; ++o) w[o] = __bfloat162float(__float2bfloat16_rn(P[OFF_W3 + o * D_H + i]));
+#pragma unroll
+    for (int o = 0; o < D_OUT; ++o) {
+        float s = h * w[o];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if ((i & 31) == 0) red[o][i >> 5] = s;
+    }
+    __syncthreads();
+    if (i < D_OUT) {
+        float s = 0;
+        for (int q = 0; q < 8; ++q) s += red[i][q];
+        const float y = s + P[OFF_B3 + i];
+        Y[b * D_OUT + i] = y;
+        float d = 0.0f;
+        if (want_grad && b < n_valid) {
+            const float e = y - T[b * D_OUT + i];
+            atomicAdd(loss, e * e / (float)(n_valid * D_OUT));
+            d = 2.0f * e / (float)(n_valid * D_OUT);
+            atomicAdd(&G[OFF_B3 + i], d);
+        }
+        dy[i] = d;
+    }
+    __syncthreads();
+    if (!want_grad) return;
+    float g = 0.0f;
+#pragma unroll
+    for (int o = 0; o < D_OUT; ++o) {
+        atomicAdd(&G[OFF_W3 + o * D_H + i], dy[o] * h);
+        g += dy[o] * w[o];
+    }
+    const bf16 z = __float2bfloat16_rn(h > 0.0f ? g : 0.0f);
+    dZ2[(size_t)b * D_H + i] = z;
+    dZ2T[(size_t)i * Mb + b] = z;
+}
+
+// bias gradient: db[j] = sum over the batch of dZ^T[j][b]  (one warp per j)
+__global__ void bias_grad_kernel(const bf16 *__restrict__ dZT, int Mb, int n_valid, float *__restrict__ db, int n)
+{
+    const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= n) return;
+    float s = 0.0f;
+    for (int b = lane; b < n_valid; b += 32) s += __bfloat162float(dZT[(size_t)j * Mb + b]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) db[j] = s;
+}
+
+// XT[c][b] = X[b][c]
+__global__ void transpose_kernel(const bf16 *__restrict__ X, int rows, int cols, bf16 *__restrict__ XT)
+{
+    __shared__ bf16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        t[i][threadIdx.x] = (r < rows && c < cols) ? X[(size_t)r * cols + c] : __float2bfloat16_rn(0.0f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) XT[(size_t)c * rows + r] = t[threadIdx.x][i];
+    }
+}
+
+// Adam (Kingma & Ba) on the FP32 master parameters; refreshes BF16 copies.
+__global__ void adam_kernel(float *__restrict__ P, const float *__restrict__ G, float *__restrict__ Mm,
+                            float *__restrict__ Vv, float lr, float b1, float b2, float eps, float c1, float c2,
+                            bf16 *__restrict__ W1b, bf16 *__restrict__ W2b, bf16 *__restrict__ W2bT)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N_PARAMS; i += (size_t)gridDim.x * blockDim.x) {
+        const float g = G[i];
+        const float m = b1 * Mm[i] + (1.0f - b1) * g;
+        const float v = b2 * Vv[i] + (1.0f - b2) * g * g;
+        Mm[i] = m;
+        Vv[i] = v;
+        const float p = P[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+        P[i] = p;
+        const bf16 pb = __float2bfloat16_rn(p);
+        if (i < OFF_B1) {
+            W1b[i] = pb;
+        } else if (i >= OFF_W2 && i < OFF_B2) {
+            const size_t q = i - OFF_W2, r = q / D_H, c = q % D_H;
+            W2b[q] = pb;
+            W2bT[c * D_H + r] = pb;
+        }
+    }
+}
+
+__global__ void refresh_bf16_kernel(const float *__restrict__ P, bf16 *__restrict__ W1b, bf16 *__restrict__ W2b,
+                                    bf16 *__restrict__ W2bT)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < OFF_B2; i += (size_t)gridDim.x * blockDim.x) {
+        const bf16 pb = __float2bfloat16_rn(P[i]);
+        if (i < OFF_B1) {
+            W1b[i] = pb;
+        } else if (i >= OFF_W2) {
+            const size_t q = i - OFF_W2, r = q / D_H, c = q % D_H;
+            W2b[q] = pb;
+            W2bT[c * D_H + r] = pb;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tensor maps
+// ---------------------------------------------------------------------------
+
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled get_encoder()
+{
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// K-major BF16 matrix [rows][cols] (cols = K contiguous), box 64 x box_rows, 128-byte swizzle
+bool make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int box_rows)
+{
+    EncodeTiled enc = get_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)tc::kBK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+struct rt_mlp {
+    cudaStream_t s = nullptr;
+    float *P = nullptr, *G = nullptr, *Mm = nullptr, *Vv = nullptr;
+    bf16 *W1b = nullptr, *W2b = nullptr, *W2bT = nullptr;
+    bf16 *X = nullptr, *XT = nullptr, *H1 = nullptr, *H1T = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ2T = nullptr,
+         *dZ1T = nullptr;
+    float *T = nullptr, *Y = nullptr, *loss = nullptr;
+    int *err = nullptr;
+    int64_t steps = 0;
+    // tensor maps (fixed buffers)
+    CUtensorMap mX, mW1, mH1, mW2, mdZ2T, mH1T, mdZ2, mW2T, mdZ1T, mXT;
+    std::string msg;
+};
+
+namespace {
+
+rt_status mfail(rt_mlp *m, rt_status s, const std::string &msg)
+{
+    if (m) m->msg = msg;
+    return s;
+}
+
+#define MC(m, call)                                                                                   \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return mfail(m, e_ == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA,               \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+    } while (0)
+
+template <class Epi>
+cudaError_t run_gemm(rt_mlp *m, const CUtensorMap &A, const CUtensorMap &B, int M, int N, int K, const Epi &epi)
+{
+    const size_t smem = tc::Smem<kBN>::kBytes;
+    static bool attr = false;
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    (void)attr;
+    dim3 grid(N / kBN, M / tc::kBM);
+    gemm_kernel<Epi><<<grid, 128, smem, m->s>>>(A, B, K, epi, m->err);
+    return cudaGetLastError();
+}
+
+rt_status check_err(rt_mlp *m)
+{
+    int e = 0;
+    MC(m, cudaMemcpyAsync(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->s));
+    MC(m, cudaStreamSynchronize(m->s));
+    if (e) return mfail(m, RT_ERR_TIMEOUT, "a tensor-core GEMM gave up waiting (code " + std::to_string(e) + ")");
+    return RT_OK;
+}
+
+// forward (and, with T, backward) of Mb rows already in m->X (n_valid real rows)
+rt_status fwd_bwd(rt_mlp *m, int Mb, int n_valid, bool grad)
+{
+    EpiReluBias e1{m->P + OFF_B1, m->H1, D_H, grad ? m->H1T : nullptr, MAXB};
+    MC(m, run_gemm(m, m->mX, m->mW1, Mb, D_H, D_IN, e1));
+    EpiReluBias e2{m->P + OFF_B2, m->H2, D_H, nullptr, 0};
+    MC(m, run_gemm(m, m->mH1, m->mW2, Mb, D_H, D_H, e2));
+    if (grad) {
+        MC(m, cudaMemsetAsync(m->G, 0, N_PARAMS * sizeof(float), m->s));
+        MC(m, cudaMemsetAsync(m->loss, 0, sizeof(float), m->s));
+    }
+    head_kernel<<<Mb, D_H, 0, m->s>>>(m->H2, m->P, m->T, n_valid, m->Y, m->G, m->dZ2, m->dZ2T, m->loss, MAXB,
+                                      grad ? 1 : 0);
+    MC(m, cudaGetLastError());
+    if (!grad) return RT_OK;
+    EpiStore s2{m->G + OFF_W2, D_H};
+    MC(m, run_gemm(m, m->mdZ2T, m->mH1T, D_H, D_H, MAXB, s2));
+    EpiMaskT mk{m->H1, D_H, m->dZ1T, MAXB};
+    MC(m, run_gemm(m, m->mdZ2, m->mW2T, Mb, D_H, D_H, mk));
+    EpiStore s1{m->G + OFF_W1, D_IN};
+    MC(m, run_gemm(m, m->mdZ1T, m->mXT, D_H, D_IN, MAXB, s1));
+    bias_grad_kernel<<<D_H / 8, 256, 0, m->s>>>(m->dZ1T, MAXB, n_valid, m->G + OFF_B1, D_H);
+    bias_grad_kernel<<<D_H / 8, 256, 0, m->s>>>(m->dZ2T, MAXB, n_valid, m->G + OFF_B2, D_H);
+    MC(m, cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status load_batch(rt_mlp *m, const void *x, const float *t, int n, int Mb)
+{
+    MC(m, cudaMemsetAsync(m->X, 0, (size_t)MAXB * D_IN * 2, m->s));
+    MC(m, cudaMemcpyAsync(m->X, x, (size_t)n * D_IN * 2, cudaMemcpyDefault, m->s));
+    if (t) {
+        MC(m, cudaMemsetAsync(m->T, 0, (size_t)MAXB * D_OUT * 4, m->s));
+        MC(m, cudaMemcpyAsync(m->T, t, (size_t)n * D_OUT * 4, cudaMemcpyDefault, m->s));
+        // X^T for the weight gradient of the first layer (all MAXB columns; padding is zero)
+        dim3 g(D_IN / 32, MAXB / 32), b(32, 8);
+        transpose_kernel<<<g, b, 0, m->s>>>(m->X, MAXB, D_IN, m->XT);
+        MC(m, cudaGetLastError());
+        // dZ rows of padded batch entries must be zero: cleared here, left zero by the head kernel
+        MC(m, cudaMemsetAsync(m->dZ2, 0, (size_t)MAXB * D_H * 2, m->s));
+        MC(m, cudaMemsetAsync(m->dZ2T, 0, (size_t)MAXB * D_H * 2, m->s));
+    }
+    (void)Mb;
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rt_status rt_mlp_create(rt_mlp **out, void *cuda_stream)
+{
+    if (!out) return RT_ERR_INVALID;
+    *out = nullptr;
+    rt_mlp *m = new rt_mlp();
+    m->s = static_cast<cudaStream_t>(cuda_stream);
+    auto A = [&](auto **p, size_t n) {
+        cudaError_t e = cudaMalloc((void **)p, n);
+        if (e == cudaSuccess) e = cudaMemset(*p, 0, n);
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = A(&m->P, N_PARAMS * 4);
+    if (e == cudaSuccess) e = A(&m->G, N_PARAMS * 4);
+    if (e == cudaSuccess) e = A(&m->Mm, N_PARAMS * 4);
+    if (e == cudaSuccess) e = A(&m->Vv, N_PARAMS * 4);
+    if (e == cudaSuccess) e = A(&m->W1b, (size_t)D_H * D_IN * 2);
+    if (e == cudaSuccess) e = A(&m->W2b, (size_t)D_H * D_H * 2);
+    if (e == cudaSuccess) e = A(&m->W2bT, (size_t)D_H * D_H * 2);
+    if (e == cudaSuccess) e = A(&m->X, (size_t)MAXB * D_IN * 2);
+    if (e == cudaSuccess) e = A(&m->XT, (size_t)MAXB * D_IN * 2);
+    if (e == cudaSuccess) e = A(&m->H1, (size_t)MAXB * D_H * 2);
+    if (e == cudaSuccess) e = A(&m->H1T, (size_t)MAXB * D_H * 2);
+    if (e == cudaSuccess) e = A(&m->H2, (size_t)MAXB * D_H * 2);
+    if (e == cudaSuccess) e = A(&m->dZ2, (size_t)MAXB * D_H * 2);
+    if (e == cudaSuccess) e = A(&m->dZ2T, (size_t)MAXB * D_H * 2);
+    if (e == cudaSuccess) e = A(&m->dZ1T, (size_t)MAXB * D_H * 2);
+    if (e == cudaSuccess) e = A(&m->T, (size_t)MAXB * D_OUT * 4);
+    if (e == cudaSuccess) e = A(&m->Y, (size_t)MAXB * D_OUT * 4);
+    if (e == cudaSuccess) e = A(&m->loss, 4);
+    if (e == cudaSuccess) e = A(&m->err, 4);
+    if (e != cudaSuccess) {
+        rt_mlp_destroy(m);
+        return e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA;
+    }
+    bool ok = make_map(&m->mX, m->X, MAXB, D_IN, tc::kBM) && make_map(&m->mW1, m->W1b, D_H, D_IN, kBN) &&
+              make_map(&m->mH1, m->H1, MAXB, D_H, tc::kBM) && make_map(&m->mW2, m->W2b, D_H, D_H, kBN) &&
+              make_map(&m->mdZ2T, m->dZ2T, D_H, MAXB, tc::kBM) && make_map(&m->mH1T, m->H1T, D_H, MAXB, kBN) &&
+              make_map(&m->mdZ2, m->dZ2, MAXB, D_H, tc::kBM) && make_map(&m->mW2T, m->W2bT, D_H, D_H, kBN) &&
+              make_map(&m->mdZ1T, m->dZ1T, D_H, MAXB, tc::kBM) && make_map(&m->mXT, m->XT, D_IN, MAXB, kBN);
+    if (!ok) {
+        rt_mlp_destroy(m);
+        return RT_ERR_CUDA;
+    }
+    *out = m;
+    return RT_OK;
+}
+
+rt_status rt_mlp_set_params(rt_mlp *m, const float *params, size_t n)
+{
+    if (!m || !params) return RT_ERR_INVALID;
+    if (n != N_PARAMS) return mfail(m, RT_ERR_INVALID, "expected 1836291 parameters");
+    MC(m, cudaMemcpyAsync(m->P, params, N_PARAMS * 4, cudaMemcpyDefault, m->s));
+    MC(m, cudaMemsetAsync(m->Mm, 0, N_PARAMS * 4, m->s));
+    MC(m, cudaMemsetAsync(m->Vv, 0, N_PARAMS * 4, m->s));
+    refresh_bf16_kernel<<<512, 256, 0, m->s>>>(m->P, m->W1b, m->W2b, m->W2bT);
+    MC(m, cudaGetLastError());
+    m->steps = 0;
+    MC(m, cudaStreamSynchronize(m->s));
+    return RT_OK;
+}
+
+rt_status rt_mlp_get_params(rt_mlp *m, float *params, size_t n)
+{
+    if (!m || !params) return RT_ERR_INVALID;
+    if (n != N_PARAMS) return mfail(m, RT_ERR_INVALID, "expected 1836291 parameters");
+    MC(m, cudaMemcpyAsync(params, m->P, N_PARAMS * 4, cudaMemcpyDefault, m->s));
+    MC(m, cudaStreamSynchronize(m->s));
+    return RT_OK;
+}
+
+rt_status rt_mlp_forward(rt_mlp *m, const void *x_bf16, int32_t n, float *y)
+{
+    if (!m || !x_bf16 || !y) return RT_ERR_INVALID;
+    if (n < 1 || n > MAXB) return mfail(m, RT_ERR_INVALID, "n must be in 1..256");
+    const int Mb = n <= 128 ? 128 : 256;
+    rt_status s = load_batch(m, x_bf16, nullptr, n, Mb);
+    if (s != RT_OK) return s;
+    if ((s = fwd_bwd(m, Mb, n, false)) != RT_OK) return s;
+    MC(m, cudaMemcpyAsync(y, m->Y, (size_t)n * D_OUT * 4, cudaMemcpyDefault, m->s));
+    return check_err(m);
+}
+
+rt_status rt_mlp_gradients(rt_mlp *m, const void *x_bf16, const float *t, int32_t n, float *grads, float *loss)
+{
+    if (!m || !x_bf16 || !t) return RT_ERR_INVALID;
+    if (n < 1 || n > MAXB) return mfail(m, RT_ERR_INVALID, "n must be in 1..256");
+    rt_status s = load_batch(m, x_bf16, t, n, MAXB);
+    if (s != RT_OK) return s;
+    if ((s = fwd_bwd(m, MAXB, n, true)) != RT_OK) return s;
+    if (grads) MC(m, cudaMemcpyAsync(grads, m->G, N_PARAMS * 4, cudaMemcpyDefault, m->s));
+    if (loss) MC(m, cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDefault, m->s));
+    return check_err(m);
+}
+
+rt_status rt_mlp_train_step(rt_mlp *m, const void *x_bf16, const float *t, int32_t n, double lr, float *loss)
+{
+    rt_status s = rt_mlp_gradients(m, x_bf16, t, n, nullptr, nullptr);
+    if (s != RT_OK) return s;
+    m->steps += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)m->steps), c2 = 1.0f - powf(b2, (float)m->steps);
+    adam_kernel<<<1024, 256, 0, m->s>>>(m->P, m->G, m->Mm, m->Vv, (float)lr, b1, b2, 1e-8f, c1, c2, m->W1b, m->W2b,
+                                        m->W2bT);
+    MC(m, cudaGetLastError());
+    if (loss) MC(m, cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDefault, m->s));
+    MC(m, cudaStreamSynchronize(m->s));
+    return RT_OK;
+}
+
+const char *rt_mlp_last_error(rt_mlp *m) { return m ? m->msg.c_str() : ""; }
+
+void rt_mlp_destroy(rt_mlp *m)
+{
+    if (!m) return;
+    if (m->s) cudaStreamSynchronize(m->s);
+    void *ps[] = {m->P, m->G, m->Mm, m->Vv, m->W1b, m->W2b, m->W2bT, m->X, m->XT, m->H1, m->H1T, m->H2,
+                  m->dZ2, m->dZ2T, m->dZ1T, m->T, m->Y, m->loss, m->err};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    delete m;
+}
+
+}  // extern "C"

@@ -39,6 +39,11 @@ __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const Pa
     const CamGeom &cg = g.cam[it.cam];
     const ConvConsts k = conv_consts(g.matrix);
     for (int i = threadIdx.x; i < 768; i += blockDim.x) sh[i] = 0;
+    {
+        const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
+        for (size_t i = tid; i < a.clear_u32_n; i += nt) a.clear_u32[i] = 0u;
+        for (size_t i = tid; i < a.clear_u64_n; i += nt) a.clear_u64[i] = 0ull;
+    }
     __syncthreads();
 
     const int upr = a.S / kUnitCols;

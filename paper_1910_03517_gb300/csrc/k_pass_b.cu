@@ -16,6 +16,8 @@
 // Histograms: 3 channels x 256 bins x 32 lane-private copies of u32 in
 // shared memory (96 KB); lane l only ever adds to copy l, so a warp's 32
 // shared atomics always hit 32 distinct banks and 32 distinct words.
+#include <cuda_bf16.h>
+
 #include "rt_internal.cuh"
 #include "pixel.cuh"
 
@@ -38,6 +40,27 @@ __device__ __forceinline__ void red_shared_inc(uint32_t addr)
 
 // Apply constants of one row for the per-camera gain fit: t = a_q * vbits + cq
 struct RowGain { uint32_t aq[3], cq[3]; };
+
+// Two conversions' rounding step in one packed FP32x2 FMA:
+// bits of (2^23 + 255 x) for x = z0, z1 (each already saturated to [0, 1]).
+__device__ __forceinline__ void magic2(float z0, float z1, uint32_t &b0, uint32_t &b1)
+{
+    asm("{\n .reg .b64 a, k, m, r;\n"
+        " mov.b64 a, {%2, %3};\n"
+        " mov.b64 k, {%4, %4};\n"
+        " mov.b64 m, {%5, %5};\n"
+        " fma.rn.f32x2 r, a, k, m;\n"
+        " mov.b64 {%0, %1}, r;\n}\n"
+        : "=r"(b0), "=r"(b1) : "f"(z0), "f"(z1), "f"(255.0f), "f"(kMagic));
+}
+
+// Pack byte 2 of four values into one word (t0 lowest): three PRMTs.
+__device__ __forceinline__ uint32_t pack4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3)
+{
+    const uint32_t lo = __byte_perm(t0, t1, 0x0062u);   // [t0.2, t1.2, -, -]
+    const uint32_t hi = __byte_perm(t2, t3, 0x6200u);   // [-, -, t2.2, t3.2]
+    return __byte_perm(lo, hi, 0x7610u);
+}
 
 __device__ __forceinline__ RowGain row_gain(const int32_t *__restrict__ q16, int cam, int j, int B)
 {
@@ -69,9 +92,40 @@ __device__ __forceinline__ uint32_t apply_seam(const CamGeom &cg, const int32_t 
     return (uint32_t)t;
 }
 
-template <int FIT, bool STATS, bool FULL>
+// Thumbnail cell sums of one row's 16 converted pixels (vbits vb[i][c]):
+// cell (i, j) covers columns [floor(i W/64), floor((i+1) W/64)) and rows
+// [floor(j H/36), floor((j+1) H/36)); a unit inside one cell adds three
+// sums, a unit across cells adds per pixel.  th: shared [36][64][3] u32.
+template <bool FULL>
+__device__ __forceinline__ void thumb_row(uint32_t *th, const CamGeom &cg, int y, int x0, int nvalid,
+                                          const uint32_t (&vb)[kUnitCols][3])
+{
+    const int cy = block_of_row(y, cg.H, RT_THUMB_H);
+    const int xl = x0 + (FULL ? kUnitCols : nvalid) - 1;
+    const int c0 = (int)(((x0 + 1) * RT_THUMB_W - 1) / cg.W), c1 = (int)(((xl + 1) * RT_THUMB_W - 1) / cg.W);
+    uint32_t *row = th + cy * RT_THUMB_W * 3;
+    if (c0 == c1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            uint32_t sum = 0;
+#pragma unroll
+            for (int i = 0; i < kUnitCols; ++i)
+                if (FULL || i < nvalid) sum += vb[i][c] - kMagicBits;
+            atomicAdd(row + c0 * 3 + c, sum);
+        }
+    } else {
+        for (int i = 0; i < (FULL ? kUnitCols : nvalid); ++i) {
+            const int cx = (int)(((x0 + i + 1) * RT_THUMB_W - 1) / cg.W);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(row + cx * 3 + c, vb[i][c] - kMagicBits);
+        }
+    }
+}
+
+template <int FIT, bool STATS, bool FULL, bool THUMBS>
 __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, int ux, const ConvConsts &k,
-                                          const int32_t *__restrict__ q16, int B, uint32_t hbase)
+                                          const int32_t *__restrict__ q16, int B, uint32_t hbase, uint32_t *th,
+                                          bool seg, uint32_t sa0, uint32_t sa1, uint32_t sa2)
 {
     const int x0 = ux * kUnitCols;
     const int y0 = rp * 2;
@@ -82,48 +136,76 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
     const uint32_t yw[2][4] = {{Y0.x, Y0.y, Y0.z, Y0.w}, {Y1.x, Y1.y, Y1.z, Y1.w}};
     const uint32_t uvw[4] = {UV.x, UV.y, UV.z, UV.w};
     const int nvalid = FULL ? kUnitCols : (cg.W - x0);
-    int jr[2];
-    jr[0] = block_of_row(y0, cg.H, B);
-    jr[1] = block_of_row(y0 + 1, cg.H, B);
+    int jr[2] = {0, 0};
     RowGain rg[2];
     if (FIT == RT_FIT_GLOBAL) {
-        rg[0] = row_gain(q16, cam, jr[0], B);
-        rg[1] = (jr[1] == jr[0]) ? rg[0] : row_gain(q16, cam, jr[1], B);
+        if (seg) {
+            // one block: the camera's gains, from the segment
+            rg[0].aq[0] = sa0; rg[0].aq[1] = sa1; rg[0].aq[2] = sa2;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) rg[0].cq[c] = 32768u - rg[0].aq[c] * kMagicBits;
+            rg[1] = rg[0];
+        } else {
+            jr[0] = block_of_row(y0, cg.H, B);
+            jr[1] = block_of_row(y0 + 1, cg.H, B);
+            rg[0] = row_gain(q16, cam, jr[0], B);
+            rg[1] = (jr[1] == jr[0]) ? rg[0] : row_gain(q16, cam, jr[1], B);
+        }
+    } else {
+        jr[0] = block_of_row(y0, cg.H, B);
+        jr[1] = block_of_row(y0 + 1, cg.H, B);
     }
     uint32_t ow[2][12];
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int i = 0; i < 12; ++i) ow[r][i] = 0u;
+    uint32_t tv[THUMBS ? 2 : 1][THUMBS ? kUnitCols : 1][3];
 
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        const float Uf = byte_f(uvw[p >> 1], (p & 1) * 2);
-        const float Vf = byte_f(uvw[p >> 1], (p & 1) * 2 + 1);
-        const float cz[3] = {fmaf(Vf, k.krv, k.c_r0), fmaf(Uf, k.kgu, fmaf(Vf, k.kgv, k.c_g0)),
-                             fmaf(Uf, k.kbu, k.c_b0)};
+    for (int g4 = 0; g4 < 4; ++g4) {                  // pixels 4 g4 .. 4 g4 + 3
+        float cz[2][3];
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
+        for (int h = 0; h < 2; ++h) {                 // chroma pairs 2 g4, 2 g4 + 1
+            const float Uf = byte_f(uvw[g4], 2 * h);
+            const float Vf = byte_f(uvw[g4], 2 * h + 1);
+            cz[h][0] = fmaf(Vf, k.krv, k.c_r0);
+            cz[h][1] = fmaf(Uf, k.kgu, fmaf(Vf, k.kgv, k.c_g0));
+            cz[h][2] = fmaf(Uf, k.kbu, k.c_b0);
+        }
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int i = 2 * p + q;
-                if (!FULL && i >= nvalid) continue;
-                const float Yf = byte_f(yw[r][i >> 2], i & 3);
+        for (int r = 0; r < 2; ++r) {
+            uint32_t t[12];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = 4 * g4 + q;
+                const float Yf = byte_f(yw[r][g4], q);
+                float z[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) z[c] = __saturatef(fmaf(Yf, k.ky, cz[q >> 1][c]));
+                uint32_t vb[3], dummy;
+                magic2(z[0], z[1], vb[0], vb[1]);
+                magic2(z[2], z[2], vb[2], dummy);
+                (void)dummy;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const uint32_t vb = zbits(Yf, k.ky, cz[c]);
-                    if (STATS) red_shared_inc(hbase + vb * 128u + (uint32_t)c * 32768u);
-                    uint32_t t;
+                    if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vb[c];
+                    const bool live = FULL || i < nvalid;
+                    if (STATS && live) red_shared_inc(hbase + vb[c] * 128u + (uint32_t)c * 32768u);
+                    uint32_t tt;
                     if (FIT == RT_FIT_GLOBAL) {
-                        t = rg[r].aq[c] * vb + rg[r].cq[c];
-                        t = t > 0xFFFFFFu ? 0xFFFFFFu : t;
+                        tt = rg[r].aq[c] * vb[c] + rg[r].cq[c];
+                        tt = tt > 0xFFFFFFu ? 0xFFFFFFu : tt;
                     } else {
-                        t = apply_seam(cg, q16, cam, jr[r], B, x0 + i, c, vb);
+                        tt = apply_seam(cg, q16, cam, jr[r], B, x0 + (live ? i : 0), c, vb[c]);
                     }
-                    const int b = 3 * i + c;
-                    ow[r][b >> 2] = put_byte2(ow[r][b >> 2], t, b & 3);
+                    t[3 * q + c] = tt;
                 }
             }
+            ow[r][3 * g4 + 0] = pack4(t[0], t[1], t[2], t[3]);
+            ow[r][3 * g4 + 1] = pack4(t[4], t[5], t[6], t[7]);
+            ow[r][3 * g4 + 2] = pack4(t[8], t[9], t[10], t[11]);
+        }
+    }
+    if constexpr (THUMBS) {
+        thumb_row<FULL>(th, cg, y0, x0, nvalid, tv[0]);
+        thumb_row<FULL>(th, cg, y0 + 1, x0, nvalid, tv[1]);
     }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -139,9 +221,9 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
     }
 }
 
-template <int FIT, bool STATS, bool FULL>
+template <int FIT, bool STATS, bool FULL, bool THUMBS>
 __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, int ux,
-                                          const int32_t *__restrict__ q16, int B, uint32_t hbase)
+                                          const int32_t *__restrict__ q16, int B, uint32_t hbase, uint32_t *th)
 {
     const int x0 = ux * kUnitCols;
     const int y0 = rp * 2;
@@ -162,10 +244,12 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
         const int j = block_of_row(y0 + r, cg.H, B);
         RowGain rg;
         if (FIT == RT_FIT_GLOBAL) rg = row_gain(q16, cam, j, B);
+        uint32_t tv[THUMBS ? kUnitCols : 1][3];
 #pragma unroll
         for (int i = 0; i < kUnitCols; ++i) {
             if (!FULL && i >= nvalid) continue;
             const uint32_t vb = mono_bits((w[i >> 1] >> (16 * (i & 1))) & 0xFFFFu, cg.shift);
+            if (THUMBS) tv[THUMBS ? i : 0][0] = tv[THUMBS ? i : 0][1] = tv[THUMBS ? i : 0][2] = vb;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 if (STATS) red_shared_inc(hbase + vb * 128u + (uint32_t)c * 32768u);
@@ -180,6 +264,7 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
                 ow[r][bb >> 2] = put_byte2(ow[r][bb >> 2], t, bb & 3);
             }
         }
+        if constexpr (THUMBS) thumb_row<FULL>(th, cg, y0 + r, x0, nvalid, tv);
     }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -197,10 +282,13 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
 
 constexpr int kHistWords = 3 * 256 * kHistLanes;
 
-template <int FIT, bool STATS>
-__global__ void __launch_bounds__(512, 2) pass_b_kernel(const ArrayGeom g, const PassBArgs a)
+constexpr int kThumbWords = RT_THUMB_H * RT_THUMB_W * 3;
+
+template <int FIT, bool STATS, bool THUMBS>
+__global__ void __launch_bounds__(THUMBS ? 512 : 1024, 1) pass_b_kernel(const ArrayGeom g, const PassBArgs a)
 {
     extern __shared__ uint32_t sh[];
+    uint32_t *th = sh + (STATS ? kHistWords : 0);   // [36][64][3] cell sums (THUMBS)
     const int tid = threadIdx.x;
     const ConvConsts k = conv_consts(g.matrix);
     uint32_t ub = (uint32_t)(((unsigned long long)blockIdx.x * g.units_total) / gridDim.x);
@@ -213,24 +301,57 @@ __global__ void __launch_bounds__(512, 2) pass_b_kernel(const ArrayGeom g, const
         const CamGeom &cg = g.cam[cam];
         const uint32_t cam_end = cam + 1 < g.K ? g.cam[cam + 1].unit_base : g.units_total;
         const uint32_t se = ue < cam_end ? ue : cam_end;
-        if (STATS) {
+        if (STATS || THUMBS) {
             uint4 *s4 = reinterpret_cast<uint4 *>(sh);
-            for (int i = tid; i < kHistWords / 4; i += blockDim.x) s4[i] = make_uint4(0, 0, 0, 0);
+            const int words = (STATS ? kHistWords : 0) + (THUMBS ? kThumbWords : 0);
+            for (int i = tid; i < words / 4; i += blockDim.x) s4[i] = make_uint4(0, 0, 0, 0);
             __syncthreads();
         }
-        const uint32_t upr = cg.upr;
+        const int upr = (int)cg.upr;
         const int full_units = cg.W / kUnitCols;
-        for (uint32_t u = ub + tid; u < se; u += blockDim.x) {
-            const uint32_t local = u - cg.unit_base;
-            const int rp = (int)(local / upr);
-            const int ux = (int)(local - (uint32_t)rp * upr);
+        // per-camera gains hoisted out of the unit loop when there is one block
+        const bool seg = FIT == RT_FIT_GLOBAL && g.B == 1;
+        uint32_t sa0 = 0, sa1 = 0, sa2 = 0;
+        if (seg) {
+            const int32_t *m = a.q16 + (size_t)cam * 2 * 6;
+            sa0 = (uint32_t)__ldg(m);
+            sa1 = (uint32_t)__ldg(m + 2);
+            sa2 = (uint32_t)__ldg(m + 4);
+        }
+        // (row pair, unit) of this thread's first unit, then stepped by blockDim
+        const int first = (int)(ub - cg.unit_base) + tid;
+        int rp = first / upr, ux = first - rp * upr;
+        const int srp = (int)blockDim.x / upr, sux = (int)blockDim.x - srp * upr;
+        const int nloc = (int)(se - cg.unit_base);
+        for (int local = first; local < nloc; local += blockDim.x) {
             if (cg.fmt == RT_NV12) {
-                if (ux < full_units) unit_nv12<FIT, STATS, true>(cg, cam, rp, ux, k, a.q16, g.B, hbase);
-                else unit_nv12<FIT, STATS, false>(cg, cam, rp, ux, k, a.q16, g.B, hbase);
+                if (ux < full_units)
+                    unit_nv12<FIT, STATS, true, THUMBS>(cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg, sa0, sa1, sa2);
+                else
+                    unit_nv12<FIT, STATS, false, THUMBS>(cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg, sa0, sa1, sa2);
             } else {
-                if (ux < full_units) unit_mono<FIT, STATS, true>(cg, cam, rp, ux, a.q16, g.B, hbase);
-                else unit_mono<FIT, STATS, false>(cg, cam, rp, ux, a.q16, g.B, hbase);
+                if (ux < full_units) unit_mono<FIT, STATS, true, THUMBS>(cg, cam, rp, ux, a.q16, g.B, hbase, th);
+                else unit_mono<FIT, STATS, false, THUMBS>(cg, cam, rp, ux, a.q16, g.B, hbase, th);
             }
+            ux += sux;
+            rp += srp;
+            if (ux >= upr) {
+                ux -= upr;
+                ++rp;
+            }
+        }
+        if (THUMBS) {
+            __syncthreads();
+            // [36][64][3] shared -> [3][36][64] global
+            uint32_t *gt = a.thumbs + (size_t)cam * kThumbWords;
+            for (int i = tid; i < kThumbWords; i += blockDim.x) {
+                const uint32_t v = th[i];
+                if (v) {
+                    const int c = i % 3, cell = i / 3;
+                    atomicAdd(gt + c * (RT_THUMB_H * RT_THUMB_W) + cell, v);
+                }
+            }
+            if (!STATS) __syncthreads();
         }
         if (STATS) {
             __syncthreads();
@@ -248,38 +369,78 @@ __global__ void __launch_bounds__(512, 2) pass_b_kernel(const ArrayGeom g, const
     }
 }
 
-template <int FIT, bool STATS>
-cudaError_t launch_one(const ArrayGeom &g, const PassBArgs &a, int grid, int threads, size_t smem,
-                       cudaStream_t s)
+template <int FIT, bool STATS, bool THUMBS>
+cudaError_t launch_one(const ArrayGeom &g, const PassBArgs &a, int grid, int threads, cudaStream_t s)
 {
-    pass_b_kernel<FIT, STATS><<<grid, threads, STATS ? smem : 0, s>>>(g, a);
+    const size_t smem = (size_t)((STATS ? kHistWords : 0) + (THUMBS ? kThumbWords : 0)) * 4;
+    pass_b_kernel<FIT, STATS, THUMBS><<<grid, threads, smem, s>>>(g, a);
     return cudaGetLastError();
+}
+
+template <int FIT>
+cudaError_t prepare_fit()
+{
+    cudaError_t e;
+    const int full = (kHistWords + kThumbWords) * 4;
+    if ((e = cudaFuncSetAttribute(pass_b_kernel<FIT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kHistWords * 4)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(pass_b_kernel<FIT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  full)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(pass_b_kernel<FIT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kThumbWords * 4)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 }  // namespace
 
+// Surrogate input features: x[k][c][j][i] = bf16(float(sum / area / 255 - 0.5))
+// with the division done in double (cell area from the camera's size).
+__global__ void thumb_features_kernel(const ArrayGeom g, const uint32_t *__restrict__ thumbs,
+                                      __nv_bfloat16 *__restrict__ out)
+{
+    const int k = blockIdx.y;
+    const CamGeom &cg = g.cam[k];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kThumbWords; e += gridDim.x * blockDim.x) {
+        const int i = e % RT_THUMB_W, j = (e / RT_THUMB_W) % RT_THUMB_H;
+        const long long cw = ((long long)(i + 1) * cg.W) / RT_THUMB_W - ((long long)i * cg.W) / RT_THUMB_W;
+        const long long ch = ((long long)(j + 1) * cg.H) / RT_THUMB_H - ((long long)j * cg.H) / RT_THUMB_H;
+        const double v = (double)thumbs[(size_t)k * kThumbWords + e] / (double)(cw * ch) / 255.0 - 0.5;
+        out[(size_t)k * kThumbWords + e] = __float2bfloat16_rn((float)v);
+    }
+}
+
+cudaError_t launch_thumb_features(const ArrayGeom &g, const uint32_t *thumbs, void *out, cudaStream_t s)
+{
+    dim3 grid(8, g.K);
+    thumb_features_kernel<<<grid, 256, 0, s>>>(g, thumbs, static_cast<__nv_bfloat16 *>(out));
+    return cudaGetLastError();
+}
+
 cudaError_t pass_b_prepare(int threads, size_t *smem_bytes)
 {
     (void)threads;
-    const size_t smem = (size_t)kHistWords * 4;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(pass_b_kernel<RT_FIT_GLOBAL, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(pass_b_kernel<RT_FIT_SEAM_AFFINE, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    *smem_bytes = smem;
+    if ((e = prepare_fit<RT_FIT_GLOBAL>()) != cudaSuccess) return e;
+    if ((e = prepare_fit<RT_FIT_SEAM_AFFINE>()) != cudaSuccess) return e;
+    *smem_bytes = (size_t)kHistWords * 4;
     return cudaSuccess;
 }
 
 cudaError_t launch_pass_b(const ArrayGeom &g, const PassBArgs &a, int grid, int threads, size_t smem,
                           cudaStream_t s)
 {
-    const bool stats = a.frame_hist != nullptr;
-    if (g.fit_mode == RT_FIT_GLOBAL)
-        return stats ? launch_one<RT_FIT_GLOBAL, true>(g, a, grid, threads, smem, s)
-                     : launch_one<RT_FIT_GLOBAL, false>(g, a, grid, threads, smem, s);
-    return stats ? launch_one<RT_FIT_SEAM_AFFINE, true>(g, a, grid, threads, smem, s)
-                 : launch_one<RT_FIT_SEAM_AFFINE, false>(g, a, grid, threads, smem, s);
+    (void)smem;
+    const bool stats = a.frame_hist != nullptr, thumbs = a.thumbs != nullptr;
+    if (g.fit_mode == RT_FIT_GLOBAL) {
+        if (thumbs) return stats ? launch_one<RT_FIT_GLOBAL, true, true>(g, a, grid, threads, s)
+                                 : launch_one<RT_FIT_GLOBAL, false, true>(g, a, grid, threads, s);
+        return stats ? launch_one<RT_FIT_GLOBAL, true, false>(g, a, grid, threads, s)
+                     : launch_one<RT_FIT_GLOBAL, false, false>(g, a, grid, threads, s);
+    }
+    if (thumbs) return stats ? launch_one<RT_FIT_SEAM_AFFINE, true, true>(g, a, grid, threads, s)
+                             : launch_one<RT_FIT_SEAM_AFFINE, false, true>(g, a, grid, threads, s);
+    return stats ? launch_one<RT_FIT_SEAM_AFFINE, true, false>(g, a, grid, threads, s)
+                 : launch_one<RT_FIT_SEAM_AFFINE, false, false>(g, a, grid, threads, s);
 }
 
 }  // namespace rt

@@ -57,6 +57,7 @@ struct rt_handle {
     std::vector<size_t> rgb_off;
     size_t rgb_bytes = 0;
     uint32_t *frame_hist[2] = {nullptr, nullptr};
+    uint32_t *thumbs[2] = {nullptr, nullptr};
     uint32_t *strip_hist[2] = {nullptr, nullptr};
     uint32_t *strip_n[2] = {nullptr, nullptr};
     unsigned long long *strip_sum[2] = {nullptr, nullptr}, *strip_sumsq[2] = {nullptr, nullptr};
@@ -103,7 +104,9 @@ struct rt_handle {
     size_t cap_crops_n = 0;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // pass B launch shape
-    int pb_grid = 0, pb_threads = 512;
+    // one pass-B CTA per SM: 896 x 64 registers leave room for pass A and the
+    // solve of the next frame set to run beside it
+    int pb_grid = 0, pb_threads = 896;
     size_t pb_smem = 0;
     std::string err;
     size_t n_maps = 0;             // K*2*B*3*2
@@ -183,7 +186,7 @@ rt_status validate(const rt_array_params *p)
     if (p->max_crops < 0 || p->max_crops > 4096) return fail(nullptr, RT_ERR_INVALID, "max_crops must be in 0..4096");
     if (p->max_crops > 0 && (p->crop_size < 1 || p->crop_size > 4096))
         return fail(nullptr, RT_ERR_INVALID, "crop_size must be in 1..4096");
-    if (p->flags & ~(RT_FLAG_FRAME_STATS)) return fail(nullptr, RT_ERR_INVALID, "unsupported flags");
+    if (p->flags & ~(RT_FLAG_FRAME_STATS | RT_FLAG_THUMBNAILS)) return fail(nullptr, RT_ERR_INVALID, "unsupported flags");
     unsigned long long units = 0;
     for (int k = 0; k < p->num_cameras; ++k) {
         const rt_camera_desc &c = p->cams[k];
@@ -228,7 +231,7 @@ void free_all(rt_handle *h)
 {
     auto F = [](void *p) { if (p) cudaFree(p); };
     for (int i = 0; i < 2; ++i) {
-        F(h->rgb[i]); F(h->frame_hist[i]); F(h->strip_hist[i]); F(h->strip_sum[i]);
+        F(h->rgb[i]); F(h->frame_hist[i]); F(h->thumbs[i]); F(h->strip_hist[i]); F(h->strip_sum[i]);
         F(h->luma[i]); F(h->crops[i]); F(h->crop_dev[i]); F(h->stage[i]);
     }
     for (int i = 0; i < kQRing; ++i) F(h->q16[i]);
@@ -300,6 +303,8 @@ rt_status setup(rt_handle *h)
         rt_status s;
         if ((s = dalloc(h, &h->rgb[i], off)) != RT_OK) return s;
         if ((s = dalloc(h, &h->frame_hist[i], (size_t)K * 768)) != RT_OK) return s;
+        if ((p.flags & RT_FLAG_THUMBNAILS) &&
+            (s = dalloc(h, &h->thumbs[i], (size_t)K * 3 * RT_THUMB_H * RT_THUMB_W)) != RT_OK) return s;
         // histograms and counts in one allocation, sums and sums of squares in
         // another, so that the solve clears a slot with two ranges
         const size_t nb = (size_t)K * 2 * B;
@@ -392,7 +397,7 @@ rt_status setup(rt_handle *h)
     }
     // pass B launch shape: a persistent grid of all resident CTAs
     RT_CUDA(h, pass_b_prepare(h->pb_threads, &h->pb_smem));
-    h->pb_grid = h->sm_count * 2;
+    h->pb_grid = h->sm_count;
     RT_CUDA(h, cudaDeviceSynchronize());
     return RT_OK;
 }
@@ -420,6 +425,14 @@ rt_status pool_event(rt_handle *h, cudaEvent_t *e)
     }
     *e = h->ev_pool[h->ev_pool_used++];
     return RT_OK;
+}
+
+// Timing event of the profiler: inside a capture it must become an event
+// record node of the graph (an ordinary record there only expresses a
+// dependency between the captured streams).
+cudaError_t prof_record(rt_handle *h, cudaEvent_t e, cudaStream_t st)
+{
+    return h->capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
 }
 
 // Enqueue one frame set whose planes are device addresses in y[] / uv[].
@@ -463,7 +476,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
         cudaEvent_t *evs[] = {&pe.a0, &pe.a1, &pe.s1, &pe.b0, &pe.b1, &pe.c1};
         for (auto e : evs)
             if ((s = pool_event(h, e)) != RT_OK) return s;
-        RT_CUDA(h, cudaEventRecord(pe.a0, h->s_stats));
+        RT_CUDA(h, prof_record(h, pe.a0, h->s_stats));
     }
     // statistics chain: pass A -> solve
     PassAArgs pa{};
@@ -472,8 +485,11 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     pa.prev_luma = h->luma[par ^ 1]; pa.cur_luma = h->luma[par];
     pa.luma_cam_stride = (int32_t)h->luma_cam_stride;
     pa.hist = h->strip_hist[par]; pa.n = h->strip_n[par]; pa.sum = h->strip_sum[par]; pa.sumsq = h->strip_sumsq[par];
-    RT_CUDA(h, launch_pass_a(g, pa, 128, h->s_stats));
-    if (prof) RT_CUDA(h, cudaEventRecord(pe.a1, h->s_stats));
+    const size_t nb = (size_t)K * 2 * p.num_blocks;
+    pa.clear_u32 = h->strip_hist[par ^ 1]; pa.clear_u32_n = nb * 768 + nb * 3;
+    pa.clear_u64 = h->strip_sum[par ^ 1]; pa.clear_u64_n = nb * 3 * 2;
+    RT_CUDA(h, launch_pass_a(g, pa, 64, h->s_stats));
+    if (prof) RT_CUDA(h, prof_record(h, pe.a1, h->s_stats));
 
     SolveArgs sa{};
     sa.n = h->strip_n[par]; sa.sum = h->strip_sum[par]; sa.sumsq = h->strip_sumsq[par];
@@ -482,13 +498,8 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     sa.first = first ? 1 : 0; sa.alpha = p.alpha; sa.lambda = p.lambda; sa.gmin = p.gain_min; sa.gmax = p.gain_max;
     sa.n_groups = h->n_groups; sa.group_start = h->group_start; sa.group_members = h->group_members;
     sa.left_nbr = h->left_nbr; sa.right_nbr = h->right_nbr; sa.cam_H = h->cam_H;
-    const size_t nb = (size_t)K * 2 * p.num_blocks;
-    // the other slot is what pass A of the next frame set accumulates into
-    sa.clear_u32 = h->strip_hist[par ^ 1]; sa.clear_u32_n = nb * 768 + nb * 3;
-    sa.clear_u64 = h->strip_sum[par ^ 1]; sa.clear_u64_n = nb * 3 * 2;
-    sa.clear2_u32 = nullptr; sa.clear2_u32_n = 0;
     RT_CUDA(h, launch_solve(sa, h->s_stats));
-    if (prof) RT_CUDA(h, cudaEventRecord(pe.s1, h->s_stats));
+    if (prof) RT_CUDA(h, prof_record(h, pe.s1, h->s_stats));
     RT_CUDA(h, cudaEventRecord(h->ev_solved[ev], h->s_stats));
 
     // main chain: clear frame histograms -> pass B -> crops
@@ -499,18 +510,23 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
         if (first) {
             q_apply = h->q16_identity;
         } else {
+            // inside a capture the first frame set's predecessor ran before the
+            // graph starts (rt_launch_sequence orders the graph after it)
             const int evp = (int)((t + kEvRing - 1) % kEvRing);
-            RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_solved[evp], 0));
+            if (!h->capturing || t - 1 >= h->cap_t0)
+                RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_solved[evp], 0));
             q_apply = h->q16[(int)((t + kQRing - 1) % kQRing)];
         }
     }
     uint32_t *fh = (p.flags & RT_FLAG_FRAME_STATS) ? h->frame_hist[par] : nullptr;
     if (fh) RT_CUDA(h, cudaMemsetAsync(fh, 0, (size_t)K * 768 * 4, h->s_main));
+    uint32_t *th = (p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[par] : nullptr;
+    if (th) RT_CUDA(h, cudaMemsetAsync(th, 0, (size_t)K * 3 * RT_THUMB_H * RT_THUMB_W * 4, h->s_main));
     PassBArgs pb{};
-    pb.q16 = q_apply; pb.frame_hist = fh; pb.thumbs = nullptr;
-    if (prof) RT_CUDA(h, cudaEventRecord(pe.b0, h->s_main));
+    pb.q16 = q_apply; pb.frame_hist = fh; pb.thumbs = th;
+    if (prof) RT_CUDA(h, prof_record(h, pe.b0, h->s_main));
     RT_CUDA(h, launch_pass_b(g, pb, h->pb_grid, h->pb_threads, h->pb_smem, h->s_main));
-    if (prof) RT_CUDA(h, cudaEventRecord(pe.b1, h->s_main));
+    if (prof) RT_CUDA(h, prof_record(h, pe.b1, h->s_main));
     if (n_crops > 0) {
         const rt_crop *table = crop_table;
         if (!table) {
@@ -528,7 +544,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
         CropArgs ca{};
         ca.crops = table; ca.n = n_crops; ca.S = p.crop_size; ca.out = h->crops[par];
         RT_CUDA(h, launch_crops(g, ca, h->s_main));
-        if (prof) RT_CUDA(h, cudaEventRecord(pe.c1, h->s_main));
+        if (prof) RT_CUDA(h, prof_record(h, pe.c1, h->s_main));
     }
     if (prof) {
         pe.crops = n_crops > 0;
@@ -752,10 +768,23 @@ rt_status rt_get_stats(rt_handle *h, rt_stats_view *out, int32_t timeout_ms)
     out->strip_sum = reinterpret_cast<const uint64_t *>(h->strip_sum[par]);
     out->strip_sumsq = reinterpret_cast<const uint64_t *>(h->strip_sumsq[par]);
     out->frame_hist = (h->p.flags & RT_FLAG_FRAME_STATS) ? h->frame_hist[par] : nullptr;
-    out->thumbs = nullptr;
+    out->thumbs = (h->p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[par] : nullptr;
     out->num_cameras = h->p.num_cameras;
     out->num_blocks = h->p.num_blocks;
     return RT_OK;
+}
+
+rt_status rt_get_thumb_features(rt_handle *h, void *x_bf16, int32_t timeout_ms)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (!x_bf16) return fail(h, RT_ERR_INVALID, "x_bf16 is NULL");
+    if (!(h->p.flags & RT_FLAG_THUMBNAILS)) return fail(h, RT_ERR_STATE, "thumbnails are off (RT_FLAG_THUMBNAILS)");
+    if (h->t == 0) return fail(h, RT_ERR_STATE, "no frame set submitted");
+    rt_status s = wait_event(h, h->ev_done[last_ev(h)], timeout_ms);
+    if (s != RT_OK) return s;
+    RT_CUDA(h, launch_thumb_features(h->geom, h->thumbs[(int)((h->t - 1) & 1)], x_bf16, h->s_d2h));
+    RT_CUDA(h, cudaEventRecord(h->ev_tmp, h->s_d2h));
+    return wait_event(h, h->ev_tmp, timeout_ms);
 }
 
 rt_status rt_copy_out(rt_handle *h, void *dst, const void *src, size_t bytes, int32_t timeout_ms)
@@ -874,8 +903,11 @@ rt_status rt_launch_sequence(rt_handle *h)
     h->t += h->cap_n;
     const int ev = last_ev(h);
     RT_CUDA(h, cudaEventRecord(h->ev_done[ev], h->s_main));
-    // the graph ran everything up to its last frame set on the main stream
+    // the graph ran everything up to its last frame set on the main stream;
+    // events last recorded inside the capture are re-recorded after the graph
+    // so that later single submits can wait on them
     for (int i = 0; i < kEvRing; ++i) {
+        RT_CUDA(h, cudaEventRecord(h->ev_solved[i], h->s_main));
         if (i != ev) RT_CUDA(h, cudaEventRecord(h->ev_done[i], h->s_main));
         h->launched[i] = true;
         h->out_launched[i] = false;

@@ -50,6 +50,10 @@ struct PassAArgs {
     uint32_t *hist;             // [K][2][B][3][256]
     uint32_t *n;                // [K][2][B][3]
     unsigned long long *sum, *sumsq;
+    // the other slot's statistics (read by the previous solve), cleared here
+    // for the next frame set
+    uint32_t *clear_u32; size_t clear_u32_n;
+    unsigned long long *clear_u64; size_t clear_u64_n;
 };
 
 // Solve: fit + smoothing + quantisation.
@@ -68,10 +72,6 @@ struct SolveArgs {
     const int32_t *left_nbr;      // [K] camera whose right band meets my left band, -1 none
     const int32_t *right_nbr;     // [K]
     const int32_t *cam_H;         // [K]
-    // buffers to clear for the next frame set (may be null)
-    uint32_t *clear_u32; size_t clear_u32_n;
-    unsigned long long *clear_u64; size_t clear_u64_n;
-    uint32_t *clear2_u32; size_t clear2_u32_n;
 };
 
 struct CropArgs {
@@ -87,5 +87,6 @@ cudaError_t pass_b_prepare(int threads, size_t *smem_bytes);
 cudaError_t launch_pass_a(const ArrayGeom &g, const PassAArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_crops(const ArrayGeom &g, const CropArgs &a, cudaStream_t s);
+cudaError_t launch_thumb_features(const ArrayGeom &g, const uint32_t *thumbs, void *out, cudaStream_t s);
 
 }  // namespace rt

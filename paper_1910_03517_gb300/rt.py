@@ -22,13 +22,15 @@ RT_FIT_GLOBAL, RT_FIT_SEAM_AFFINE = 0, 1
 RT_SCHED_CURRENT, RT_SCHED_LAGGED = 0, 1
 RT_BT709, RT_BT601 = 0, 1
 RT_FLAG_FRAME_STATS = 1
+RT_FLAG_THUMBNAILS = 2
 RT_MAX_CAMERAS = 32
 
 # every symbol include/rt.h declares (checked by the tests)
 EXPORTS = ["rt_default_params", "rt_array_config", "rt_submit_frames", "rt_submit_frames_host",
            "rt_get_gains", "rt_get_corrected", "rt_copy_corrected", "rt_get_crops", "rt_get_stats",
            "rt_copy_out", "rt_sync", "rt_save_state", "rt_load_state", "rt_last_error", "rt_destroy",
-           "rt_stream_wait", "rt_capture_sequence", "rt_launch_sequence", "rt_profile", "rt_get_profile"]
+           "rt_stream_wait", "rt_capture_sequence", "rt_launch_sequence", "rt_profile", "rt_get_profile",
+           "rt_get_thumb_features"]
 
 c_i32, c_i64, c_dbl, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 
@@ -94,6 +96,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rt_launch_sequence.argtypes = [c_vp]
     L.rt_profile.argtypes = [c_vp, c_i32]
     L.rt_get_profile.argtypes = [c_vp, ctypes.POINTER(ProfileReport), c_i32]
+    L.rt_get_thumb_features.argtypes = [c_vp, c_vp, c_i32]
     L.rt_destroy.argtypes = [c_vp]
     L.rt_destroy.restype = None
     for name in EXPORTS:
@@ -232,7 +235,8 @@ class CameraArray:
                                      ("strip_n", v.strip_n, (K, 2, B, 3), np.uint32),
                                      ("strip_sum", v.strip_sum, (K, 2, B, 3), np.uint64),
                                      ("strip_sumsq", v.strip_sumsq, (K, 2, B, 3), np.uint64),
-                                     ("frame_hist", v.frame_hist, (K, 3, 256), np.uint32)):
+                                     ("frame_hist", v.frame_hist, (K, 3, 256), np.uint32),
+                                     ("thumbs", v.thumbs, (K, 3, 36, 64), np.uint32)):
             if not ptr:
                 out[name] = None
                 continue
@@ -284,6 +288,13 @@ class CameraArray:
         return {"frame_sets": r.frame_sets, "pass_a_ms": r.pass_a_ms, "solve_ms": r.solve_ms,
                 "pass_b_ms": r.pass_b_ms, "crops_ms": r.crops_ms}
 
+    def thumb_features(self, timeout_ms: int = 60000):
+        """BF16 device tensor [K, 6912] of the last frame set's thumbnail features."""
+        import torch
+        x = torch.empty((self.K, 6912), dtype=torch.bfloat16, device="cuda")
+        _check(self.L, self.h, self.L.rt_get_thumb_features(self.h, x.data_ptr(), timeout_ms))
+        return x
+
     def sync(self, timeout_ms: int = 60000):
         _check(self.L, self.h, self.L.rt_sync(self.h, timeout_ms))
 
@@ -301,6 +312,106 @@ class CameraArray:
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             self.L.rt_destroy(self.h)
+            self.h = c_vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# learned gain surrogate (include/rt_surrogate.h)
+# ---------------------------------------------------------------------------
+
+MLP_INPUTS = 6912
+MLP_PARAMS = 1836291
+MLP_EXPORTS = ["rt_mlp_create", "rt_mlp_set_params", "rt_mlp_get_params", "rt_mlp_forward", "rt_mlp_gradients",
+               "rt_mlp_train_step", "rt_mlp_last_error", "rt_mlp_destroy"]
+
+
+def _load_mlp(L):
+    if getattr(L, "_mlp_ready", False):
+        return
+    L.rt_mlp_create.argtypes = [ctypes.POINTER(c_vp), c_vp]
+    L.rt_mlp_set_params.argtypes = [c_vp, c_vp, c_sz]
+    L.rt_mlp_get_params.argtypes = [c_vp, c_vp, c_sz]
+    L.rt_mlp_forward.argtypes = [c_vp, c_vp, c_i32, c_vp]
+    L.rt_mlp_gradients.argtypes = [c_vp, c_vp, c_vp, c_i32, c_vp, c_vp]
+    L.rt_mlp_train_step.argtypes = [c_vp, c_vp, c_vp, c_i32, c_dbl, c_vp]
+    L.rt_mlp_last_error.argtypes = [c_vp]
+    L.rt_mlp_last_error.restype = ctypes.c_char_p
+    L.rt_mlp_destroy.argtypes = [c_vp]
+    L.rt_mlp_destroy.restype = None
+    for n in MLP_EXPORTS[:-2]:
+        getattr(L, n).restype = c_i32
+    L._mlp_ready = True
+
+
+def param_offsets():
+    """(name, offset, shape) of each tensor in the flat parameter vector."""
+    out, off = [], 0
+    for name, shape in (("W1", (256, MLP_INPUTS)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)),
+                        ("W3", (3, 256)), ("b3", (3,))):
+        n = int(np.prod(shape))
+        out.append((name, off, shape))
+        off += n
+    assert off == MLP_PARAMS
+    return out
+
+
+class GainMLP:
+    """The surrogate network (a handle of librt.so's rt_mlp)."""
+
+    def __init__(self, stream=None):
+        import torch
+        self.L = load()
+        _load_mlp(self.L)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.h = c_vp()
+        st = self.L.rt_mlp_create(ctypes.byref(self.h), c_vp(sp))
+        if st != RT_OK:
+            raise RtError(st, "rt_mlp_create failed")
+
+    def _chk(self, st):
+        if st != RT_OK:
+            raise RtError(st, self.L.rt_mlp_last_error(self.h).decode())
+
+    def set_params(self, flat: np.ndarray):
+        a = np.ascontiguousarray(flat, np.float32)
+        self._chk(self.L.rt_mlp_set_params(self.h, a.ctypes.data, a.size))
+
+    def get_params(self) -> np.ndarray:
+        a = np.zeros(MLP_PARAMS, np.float32)
+        self._chk(self.L.rt_mlp_get_params(self.h, a.ctypes.data, a.size))
+        return a
+
+    def forward(self, x):
+        import torch
+        n = x.shape[0]
+        y = torch.empty((n, 3), dtype=torch.float32, device=x.device)
+        self._chk(self.L.rt_mlp_forward(self.h, x.data_ptr(), n, y.data_ptr()))
+        return y
+
+    def gradients(self, x, t):
+        n = x.shape[0]
+        g = np.zeros(MLP_PARAMS, np.float32)
+        loss = np.zeros(1, np.float32)
+        self._chk(self.L.rt_mlp_gradients(self.h, x.data_ptr(), t.data_ptr(), n, g.ctypes.data, loss.ctypes.data))
+        return g, float(loss[0])
+
+    def train_step(self, x, t, lr: float) -> float:
+        loss = np.zeros(1, np.float32)
+        self._chk(self.L.rt_mlp_train_step(self.h, x.data_ptr(), t.data_ptr(), x.shape[0], float(lr),
+                                           loss.ctypes.data))
+        return float(loss[0])
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.rt_mlp_destroy(self.h)
             self.h = c_vp()
 
     def __del__(self):

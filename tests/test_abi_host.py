@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(L):
     assert declared, "no declarations found"
     for name in declared:
         assert hasattr(L, name), name
-    assert set(rt.EXPORTS) <= declared
+    assert set(rt.EXPORTS) | set(rt.MLP_EXPORTS) <= declared
 
 
 def test_defaults(L):

@@ -48,11 +48,13 @@ def _check_q16(q_gpu, q_orc, E):
 
 
 def run_sequence(rt, orc, wl, frames, crops_per_frame=0, crop_size=0, device_inputs=True,
-                 stats=True, check_images=True, **kw):
+                 stats=True, check_images=True, thumbs=False, **kw):
     """Submit `frames` frame sets to the GPU and the oracle, compare each."""
+    from oracle import mlp as omlp
     p = _params_for_oracle(orc, **kw)
+    flags = (rt.RT_FLAG_FRAME_STATS if stats else 0) | (rt.RT_FLAG_THUMBNAILS if thumbs else 0)
     arr = rt.CameraArray(wl.cams, max_crops=max(crops_per_frame, 0), crop_size=max(crop_size, 0),
-                         flags=rt.RT_FLAG_FRAME_STATS if stats else 0, **kw)
+                         flags=flags, **kw)
     o = orc.ArrayOracle(wl.cams, p)
     K = len(wl.cams)
     results = []
@@ -67,7 +69,13 @@ def run_sequence(rt, orc, wl, frames, crops_per_frame=0, crop_size=0, device_inp
         maps, q16 = arr.get_gains()
         st = arr.get_stats()
         r = o.step(np_frames(fs), crops=crops, crop_size=crop_size, q16_override=q16,
-                   want_frame_stats=stats)
+                   want_frame_stats=stats, want_thumbs=thumbs)
+        if thumbs:
+            assert np.array_equal(st["thumbs"], r["thumbs"]), t
+            feat = arr.thumb_features().float().cpu().numpy()
+            for k, c in enumerate(wl.cams):
+                ref = omlp.bf16_round(omlp.thumb_features(r["thumbs"][k], c.width, c.height))
+                assert np.array_equal(feat[k], ref.astype(np.float32)), (t, k)
         # statistics: bit-exact
         assert np.array_equal(st["strip_n"], r["strip_n"]), t
         assert np.array_equal(st["strip_sum"], r["strip_sum"]), t
@@ -241,3 +249,52 @@ def test_tower12_full_size(rt, orc):
 def test_uneven_array_full_size_with_crops(rt, orc):
     wl = synth.uneven_array(frames=2)
     run_sequence(rt, orc, wl, 2, crops_per_frame=8, crop_size=512, num_blocks=16)
+
+
+@pytest.mark.parametrize("kw", [{}, {"fit_mode": 1, "num_blocks": 16, "schedule": 1}])
+def test_captured_ring_matches_single_submits(rt, kw):
+    wl = synth.small_pair()
+    wl.n_crops, wl.crop_side, wl.crop_out = 5, (16, 200), 40
+    ring = 6
+    frames = [synth.frame_set(wl, t, device="cuda") for t in range(ring)]
+    crops = [synth.crop_list(wl, t) for t in range(ring)]
+    a = rt.CameraArray(wl.cams, max_crops=5, crop_size=40, **kw)
+    b = rt.CameraArray(wl.cams, max_crops=5, crop_size=40, **kw)
+    a.submit_frames(frames[0], 0, crops[0])
+    a.profile(True)
+    order = [(1 + j) % ring for j in range(ring)]
+    a.capture_sequence([frames[i] for i in order], [crops[i] for i in order])
+    a.profile(False)
+    for t in range(0, 1 + 2 * ring):
+        b.submit_frames(frames[t % ring], t, crops[t % ring])
+    a.launch_sequence()
+    a.launch_sequence()
+    ma, qa = a.get_gains()
+    mb, qb = b.get_gains()
+    assert np.array_equal(ma, mb) and np.array_equal(qa, qb)
+    for k in range(2):
+        assert torch.equal(a.get_corrected(k), b.get_corrected(k))
+    assert torch.equal(a.get_crops(), b.get_crops())
+    sa, sb = a.get_stats(), b.get_stats()
+    for name in ("strip_hist", "strip_n", "strip_sum", "frame_hist"):
+        assert np.array_equal(sa[name], sb[name]), name
+    prof = a.get_profile()
+    assert prof["frame_sets"] == ring
+    assert prof["pass_b_ms"] > 0 and prof["pass_a_ms"] > 0 and prof["solve_ms"] > 0 and prof["crops_ms"] > 0
+    # a single submit in between breaks the ring's slot alignment
+    a.submit_frames(frames[1], 13, crops[1])
+    with pytest.raises(rt.RtError) as ei:
+        a.launch_sequence()
+    assert ei.value.status == rt.RT_ERR_STATE
+    a.close()
+    b.close()
+
+
+def test_thumbnails_and_features(rt, orc):
+    run_sequence(rt, orc, synth.small_pair(), 2, thumbs=True)
+    cams = [synth.Camera(72, 38, position=0, y_pitch=80, uv_pitch=80),
+            synth.Camera(130, 76, position=1, y_pitch=144, uv_pitch=144),
+            synth.Camera(90, 20, fmt=synth.MONO16, bit_depth=12, group=1, y_pitch=192)]
+    wl = synth.Workload("ragged thumbs", cams, frames=2, seed=21)
+    run_sequence(rt, orc, wl, 2, thumbs=True, strip_width=16, min_valid=8)
+    run_sequence(rt, orc, synth.tower12(frames=1), 1, thumbs=True, stats=False)
