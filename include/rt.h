@@ -116,7 +116,8 @@ typedef struct {
 } rt_array_params;
 
 #define RT_FLAG_FRAME_STATS 1   /* whole-frame histograms of every camera (S2 iii) */
-#define RT_FLAG_THUMBNAILS 2    /* 64x36 thumbnail cell sums of every camera (surrogate input) */
+#define RT_FLAG_THUMBNAILS 2    /* 64x36 thumbnail cell sums of every camera (surrogate input);
+                                   needs every camera at least 64 x 36 pixels */
 
 /* An attention window: rectangle (x0, y0, w, h) of camera cam, inside it. */
 typedef struct { int32_t cam, x0, y0, w, h; } rt_crop;

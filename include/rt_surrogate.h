@@ -54,6 +54,19 @@ rt_status rt_mlp_gradients(rt_mlp *m, const void *x_bf16, const float *t, int32_
  * the batch; *loss (may be NULL) receives the batch loss before the step. */
 rt_status rt_mlp_train_step(rt_mlp *m, const void *x_bf16, const float *t, int32_t n, double lr, float *loss);
 
+/* Surrogate inference and its judge for the last frame set of an array
+ * (rt.h handle with per-camera gains, one block, RT_FLAG_THUMBNAILS): the
+ * thumbnail features of every camera go through the network m; the
+ * predicted log-gains are re-gauged per seam chain (the chain's mean
+ * log-gain per channel subtracted, as the fit's gauge does) and turned into
+ * gains clamped like the fit's.  Writes maps_fp64 (may be NULL; layout of
+ * rt_get_gains, (g, 0) on both sides) and *max_error (may be NULL): the
+ * largest |g_pred / g_fit - 1| over cameras and channels against the
+ * per-camera gain fit of the same frame set (before smoothing).  A caller
+ * uses the prediction while *max_error stays below its tolerance and the
+ * plain fit otherwise. */
+rt_status rt_surrogate_predict(rt_handle *h, rt_mlp *m, double *maps_fp64, double *max_error, int32_t timeout_ms);
+
 /* Text of the network's last error. */
 const char *rt_mlp_last_error(rt_mlp *m);
 

@@ -40,7 +40,15 @@ def thumb_features(sums: np.ndarray, W: int, H: int) -> np.ndarray:
 
 
 def _mm(a, b, acc32):
-    """a @ b, accumulated in float32 when acc32 (operands are BF16 values)."""
+    """a @ b, accumulated in float32 when acc32 (operands are BF16 values).
+    acc32 == "split" sums the two halves of the inner dimension separately
+    and then adds them: another valid float32 summation order, used to
+    measure how far two FP32 orders drift apart through the BF16 rounding
+    decisions (the noise floor a GPU result is compared against)."""
+    if acc32 == "split":
+        a32, b32 = np.asarray(a, np.float32), np.asarray(b, np.float32)
+        h = a32.shape[-1] // 2
+        return (a32[..., :h] @ b32[:h] + a32[..., h:] @ b32[h:]).astype(np.float64)
     if acc32:
         return (np.asarray(a, np.float32) @ np.asarray(b, np.float32)).astype(np.float64)
     return a @ b

@@ -211,6 +211,42 @@ __global__ void refresh_bf16_kernel(const float *__restrict__ P, bf16 *__restric
     }
 }
 
+// Predicted log-gains y[K][3] -> re-gauged, clamped gains per chain and the
+// judge's error against the fitted gains (maps_fit [K][2][1][3][2]).  One
+// thread per (chain, channel); single CTA.
+__global__ void surrogate_gains_kernel(const float *__restrict__ y, const int32_t *__restrict__ group_start,
+                                       const int32_t *__restrict__ group_members, int n_groups,
+                                       const double *__restrict__ maps_fit, double gmin, double gmax,
+                                       double *__restrict__ maps_out, double *__restrict__ err_out)
+{
+    __shared__ double worst[96];
+    const int t = threadIdx.x;
+    double e = 0.0;
+    if (t < n_groups * 3) {
+        const int grp = t / 3, c = t % 3;
+        const int g0 = group_start[grp], n = group_start[grp + 1] - g0;
+        double mean = 0.0;
+        for (int i = 0; i < n; ++i) mean += (double)y[group_members[g0 + i] * 3 + c];
+        mean /= n;
+        for (int i = 0; i < n; ++i) {
+            const int cam = group_members[g0 + i];
+            const double g = fmin(fmax(exp((double)y[cam * 3 + c] - mean), gmin), gmax);
+            for (int side = 0; side < 2; ++side) {
+                maps_out[((cam * 2 + side) * 3 + c) * 2] = g;
+                maps_out[((cam * 2 + side) * 3 + c) * 2 + 1] = 0.0;
+            }
+            e = fmax(e, fabs(g / maps_fit[((cam * 2) * 3 + c) * 2] - 1.0));
+        }
+    }
+    if (t < 96) worst[t] = e;
+    __syncthreads();
+    if (t == 0) {
+        double m = 0.0;
+        for (int i = 0; i < 96 && i < n_groups * 3; ++i) m = fmax(m, worst[i]);
+        *err_out = m;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // tensor maps
 // ---------------------------------------------------------------------------
@@ -461,6 +497,22 @@ rt_status rt_mlp_train_step(rt_mlp *m, const void *x_bf16, const float *t, int32
 }
 
 const char *rt_mlp_last_error(rt_mlp *m) { return m ? m->msg.c_str() : ""; }
+
+}  // extern "C"
+
+namespace rt {
+cudaError_t launch_surrogate_gains(const float *y, const int32_t *group_start, const int32_t *group_members,
+                                   int n_groups, const double *maps_fit, double gmin, double gmax, double *maps_out,
+                                   double *err_out, cudaStream_t s)
+{
+    if (n_groups * 3 > 96) return cudaErrorInvalidValue;
+    surrogate_gains_kernel<<<1, 96, 0, s>>>(y, group_start, group_members, n_groups, maps_fit, gmin, gmax, maps_out,
+                                            err_out);
+    return cudaGetLastError();
+}
+}  // namespace rt
+
+extern "C" {
 
 void rt_mlp_destroy(rt_mlp *m)
 {

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const Pa
     __shared__ uint32_t sh[3 * 256];
     const StripItem it = a.items[blockIdx.x];
     const CamGeom &cg = g.cam[it.cam];
-    const ConvConsts k = conv_consts(g.matrix);
+    const ConvConsts &k = g.conv;
     for (int i = threadIdx.x; i < 768; i += blockDim.x) sh[i] = 0;
     {
         const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
@@ -112,12 +112,12 @@ __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const Pa
         const uint32_t cnt = sh[b];
         if (cnt) atomicAdd(a.hist + slot * 256 + b, cnt);
     }
-    // moments of the three channel histograms: warp c reduces channel c
+    // moments of the three channel histograms, one warp per channel in turn
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < 3) {
+    for (int c = warp; c < 3; c += (int)(blockDim.x >> 5)) {
         unsigned long long n = 0, s = 0, ss = 0;
         for (int b = lane; b < 256; b += 32) {
-            const unsigned long long cnt = sh[warp * 256 + b];
+            const unsigned long long cnt = sh[c * 256 + b];
             n += cnt;
             s += cnt * (unsigned long long)b;
             ss += cnt * (unsigned long long)(b * b);
@@ -129,9 +129,9 @@ __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const Pa
             ss += __shfl_xor_sync(0xffffffffu, ss, o);
         }
         if (lane == 0 && n) {
-            atomicAdd(a.n + slot + warp, (uint32_t)n);
-            atomicAdd(a.sum + slot + warp, s);
-            atomicAdd(a.sumsq + slot + warp, ss);
+            atomicAdd(a.n + slot + c, (uint32_t)n);
+            atomicAdd(a.sum + slot + c, s);
+            atomicAdd(a.sumsq + slot + c, ss);
         }
     }
 }

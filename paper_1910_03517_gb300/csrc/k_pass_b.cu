@@ -125,14 +125,11 @@ __device__ __forceinline__ void thumb_row(uint32_t *th, const CamGeom &cg, int y
 template <int FIT, bool STATS, bool FULL, bool THUMBS>
 __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, int ux, const ConvConsts &k,
                                           const int32_t *__restrict__ q16, int B, uint32_t hbase, uint32_t *th,
-                                          bool seg, uint32_t sa0, uint32_t sa1, uint32_t sa2)
+                                          bool seg, uint32_t sa0, uint32_t sa1, uint32_t sa2,
+                                          const uint4 Y0, const uint4 Y1, const uint4 UV)
 {
     const int x0 = ux * kUnitCols;
     const int y0 = rp * 2;
-    const uint8_t *yp = cg.y + (size_t)y0 * cg.y_pitch + x0;
-    const uint4 Y0 = ld_stream(yp);
-    const uint4 Y1 = ld_stream(yp + cg.y_pitch);
-    const uint4 UV = ld_stream(cg.uv + (size_t)rp * cg.uv_pitch + x0);
     const uint32_t yw[2][4] = {{Y0.x, Y0.y, Y0.z, Y0.w}, {Y1.x, Y1.y, Y1.z, Y1.w}};
     const uint32_t uvw[4] = {UV.x, UV.y, UV.z, UV.w};
     const int nvalid = FULL ? kUnitCols : (cg.W - x0);
@@ -172,17 +169,25 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             uint32_t t[12];
+            // conversion of the 4 pixels: 12 saturated z, rounded two at a time
+            uint32_t vbq[4][3];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {             // pixels 2h, 2h+1 share a chroma pair
+                const float Y0f = byte_f(yw[r][g4], 2 * h), Y1f = byte_f(yw[r][g4], 2 * h + 1);
+                float z0[3], z1[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    z0[c] = __saturatef(fmaf(Y0f, k.ky, cz[h][c]));
+                    z1[c] = __saturatef(fmaf(Y1f, k.ky, cz[h][c]));
+                }
+                magic2(z0[0], z0[1], vbq[2 * h][0], vbq[2 * h][1]);
+                magic2(z1[0], z1[1], vbq[2 * h + 1][0], vbq[2 * h + 1][1]);
+                magic2(z0[2], z1[2], vbq[2 * h][2], vbq[2 * h + 1][2]);
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int i = 4 * g4 + q;
-                const float Yf = byte_f(yw[r][g4], q);
-                float z[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) z[c] = __saturatef(fmaf(Yf, k.ky, cz[q >> 1][c]));
-                uint32_t vb[3], dummy;
-                magic2(z[0], z[1], vb[0], vb[1]);
-                magic2(z[2], z[2], vb[2], dummy);
-                (void)dummy;
+                const uint32_t *vb = vbq[q];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vb[c];
@@ -290,9 +295,14 @@ __global__ void __launch_bounds__(THUMBS ? 512 : 1024, 1) pass_b_kernel(const Ar
     extern __shared__ uint32_t sh[];
     uint32_t *th = sh + (STATS ? kHistWords : 0);   // [36][64][3] cell sums (THUMBS)
     const int tid = threadIdx.x;
-    const ConvConsts k = conv_consts(g.matrix);
-    uint32_t ub = (uint32_t)(((unsigned long long)blockIdx.x * g.units_total) / gridDim.x);
-    const uint32_t ue = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * g.units_total) / gridDim.x);
+    const ConvConsts &k = g.conv;
+    // clear the accumulators the next frame set will use (other parity)
+    for (uint32_t i = blockIdx.x * blockDim.x + tid; i < a.clear_a_n; i += gridDim.x * blockDim.x) a.clear_a[i] = 0u;
+    for (uint32_t i = blockIdx.x * blockDim.x + tid; i < a.clear_b_n; i += gridDim.x * blockDim.x) a.clear_b[i] = 0u;
+    // balanced contiguous slices: q units each, the first r slices one more
+    const uint32_t q = g.units_total / gridDim.x, r = g.units_total - q * gridDim.x;
+    uint32_t ub = blockIdx.x * q + min(blockIdx.x, r);
+    const uint32_t ue = ub + q + (blockIdx.x < r ? 1u : 0u);
     int cam = 0;
     while (cam + 1 < g.K && g.cam[cam + 1].unit_base <= ub) ++cam;
     const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(sh) + (uint32_t)(tid & 31) * 4u -
@@ -323,21 +333,34 @@ __global__ void __launch_bounds__(THUMBS ? 512 : 1024, 1) pass_b_kernel(const Ar
         int rp = first / upr, ux = first - rp * upr;
         const int srp = (int)blockDim.x / upr, sux = (int)blockDim.x - srp * upr;
         const int nloc = (int)(se - cg.unit_base);
-        for (int local = first; local < nloc; local += blockDim.x) {
-            if (cg.fmt == RT_NV12) {
+        if (cg.fmt == RT_NV12) {
+            for (int local = first; local < nloc; local += blockDim.x) {
+                const uint8_t *yp = cg.y + (size_t)(2 * rp) * cg.y_pitch + ux * kUnitCols;
+                const uint4 Y0 = ld_stream(yp), Y1 = ld_stream(yp + cg.y_pitch);
+                const uint4 UV = ld_stream(cg.uv + (size_t)rp * cg.uv_pitch + ux * kUnitCols);
                 if (ux < full_units)
-                    unit_nv12<FIT, STATS, true, THUMBS>(cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg, sa0, sa1, sa2);
+                    unit_nv12<FIT, STATS, true, THUMBS>(cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg, sa0, sa1,
+                                                        sa2, Y0, Y1, UV);
                 else
-                    unit_nv12<FIT, STATS, false, THUMBS>(cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg, sa0, sa1, sa2);
-            } else {
+                    unit_nv12<FIT, STATS, false, THUMBS>(cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg, sa0, sa1,
+                                                         sa2, Y0, Y1, UV);
+                ux += sux;
+                rp += srp;
+                if (ux >= upr) {
+                    ux -= upr;
+                    ++rp;
+                }
+            }
+        } else {
+            for (int local = first; local < nloc; local += blockDim.x) {
                 if (ux < full_units) unit_mono<FIT, STATS, true, THUMBS>(cg, cam, rp, ux, a.q16, g.B, hbase, th);
                 else unit_mono<FIT, STATS, false, THUMBS>(cg, cam, rp, ux, a.q16, g.B, hbase, th);
-            }
-            ux += sux;
-            rp += srp;
-            if (ux >= upr) {
-                ux -= upr;
-                ++rp;
+                ux += sux;
+                rp += srp;
+                if (ux >= upr) {
+                    ux -= upr;
+                    ++rp;
+                }
             }
         }
         if (THUMBS) {
@@ -373,6 +396,8 @@ template <int FIT, bool STATS, bool THUMBS>
 cudaError_t launch_one(const ArrayGeom &g, const PassBArgs &a, int grid, int threads, cudaStream_t s)
 {
     const size_t smem = (size_t)((STATS ? kHistWords : 0) + (THUMBS ? kThumbWords : 0)) * 4;
+    // the thumbnail variant is compiled for at most 512 threads per CTA
+    if (THUMBS && threads > 512) threads = 512;
     pass_b_kernel<FIT, STATS, THUMBS><<<grid, threads, smem, s>>>(g, a);
     return cudaGetLastError();
 }

@@ -6,8 +6,9 @@
 //   (L_w + lambda I + 1 1^T / K_g) x = B^T W r,
 // x_k = log g_k, r = log mu^L(right camera) - log mu^R(left camera) over the
 // valid seams, w = valid fraction of the band; solved in FP64 by one warp
-// per system (tridiagonal factorisation plus a rank-two Woodbury correction,
-// see solve_global_kernel); g = clamp(exp(x)).
+// per system (continuant elimination of the chain's tridiagonal matrix and a
+// rank-one Woodbury correction for a ring, see solve_global_kernel);
+// g = clamp(exp(x)).
 // Seam affine maps: one thread per (camera, side, block, channel) matches
 // its band's mean and variance to the equal-weight mixture of the two bands
 // of its seam: a = sd_s / sd_side, b = mu_s - a mu_side.
@@ -40,109 +41,132 @@ __device__ __forceinline__ void smooth_store(const SolveArgs &a, size_t idx, dou
 __device__ __forceinline__ int block_rows(int j, int H, int B) { return (int)(((long long)(j + 1) * H) / B - ((long long)j * H) / B); }
 
 
-// One system per CTA (one warp): the GPU's FP64 units are few, so systems
-// are spread over SMs.  The chain's matrix is
-//   M = T + u u^T + v v^T,   T = L_w(chain seams) + lambda I (tridiagonal),
-//   u = 1/sqrt(K_g) (the gauge term), v = sqrt(w_c)(e_last - e_first) (the
-// ring-closing seam, absent for a linear chain),
-// so x = M^-1 rhs by the Woodbury identity from three tridiagonal solves
-// with one factorisation (Thomas; T is symmetric, diagonally dominant).
+// One system per CTA (one warp): the GPU's FP64 units are few and slow, so
+// systems are spread over SMs and the sequential part is kept short.
+//
+// The right-hand side sums to zero (every seam adds w r to one camera and
+// subtracts it from the other), so 1^T x = 0 and the gauge term 1 1^T / K_g
+// leaves the solution unchanged: x solves (L_w + lambda I) x = rhs.  For a
+// chain that matrix T is tridiagonal (diagonal d_k = lambda + w_{k-1} + w_k,
+// off-diagonals -w); a ring adds its closing seam as a rank-one term
+// v v^T, v = sqrt(w_c)(e_last - e_first), handled by the Woodbury identity.
+// T is eliminated through its continuants
+//   P_{-1} = 1, P_k = d_k P_{k-1} - w_{k-1}^2 P_{k-2},
+//   s_k = rhs_k P_{k-1} + w_{k-1} s_{k-1}          (forward, one FMA per step)
+//   x_k = s_k / P_k + (w_k P_{k-1} / P_k) x_{k+1}   (backward, one FMA per step)
+// so the divisions run on all lanes at once and only FMAs stay sequential.
 __global__ void __launch_bounds__(32) solve_global_kernel(const SolveArgs a)
 {
-    __shared__ double sw[kMaxChain], sr[kMaxChain], cp[kMaxChain];
-    __shared__ double zb[kMaxChain], zu[kMaxChain], zv[kMaxChain], x[kMaxChain];
+    __shared__ double sw[kMaxChain], srw[kMaxChain], wp[kMaxChain], rh[kMaxChain], vv[kMaxChain];
+    __shared__ double P[kMaxChain], Pp[kMaxChain], sB[kMaxChain], sV[kMaxChain];
+    __shared__ double aB[kMaxChain], aV[kMaxChain], bt[kMaxChain], xb[kMaxChain], xv[kMaxChain];
     __shared__ int sb[kMaxChain];
     const int lane = threadIdx.x;
     const int sys = blockIdx.x;
     const int c = sys % 3, j = (sys / 3) % a.B, grp = sys / (3 * a.B);
     const int g0 = a.group_start[grp];
     const int n = a.group_start[grp + 1] - g0;
-    // the seam whose left camera is member `lane`: weight and log-mean difference
-    sw[lane] = 0.0;
-    sr[lane] = 0.0;
-    sb[lane] = -1;
+    // 1. the seam whose left camera is member `lane`: weight w and w * r,
+    //    r = log mu^L - log mu^R (one logarithm of the ratio)
+    double w = 0.0, wr = 0.0;
+    int bpos = -1;
     if (lane < n) {
         const int kl = a.group_members[g0 + lane];
         const int kr = a.right_nbr[kl];
         if (kr >= 0 && kr != kl) {
-            int bpos = -1;
             for (int q = 0; q < n; ++q)
                 if (a.group_members[g0 + q] == kr) bpos = q;
             const size_t iR = ((size_t)(kl * 2 + 1) * a.B + j) * 3 + c;
             const size_t iL = ((size_t)(kr * 2 + 0) * a.B + j) * 3 + c;
-            const double nR = (double)a.n[iR], nL = (double)a.n[iL];
-            if (bpos >= 0 && nR >= a.min_valid && nL >= a.min_valid) {
-                const double muR = fmax((double)a.sum[iR] / nR, 1.0);
-                const double muL = fmax((double)a.sum[iL] / nL, 1.0);
+            const uint32_t nR = a.n[iR], nL = a.n[iL];
+            if (bpos >= 0 && nR >= (uint32_t)a.min_valid && nL >= (uint32_t)a.min_valid) {
+                const unsigned long long sR = a.sum[iR], sL = a.sum[iL];
+                double ratio;
+                if (sR >= nR && sL >= nL)      // both means >= 1: exact integer products
+                    ratio = (double)(sL * nR) / (double)(sR * nL);
+                else
+                    ratio = fmax((double)sL / (double)nL, 1.0) / fmax((double)sR / (double)nR, 1.0);
                 const int rows = min(block_rows(j, a.cam_H[kl], a.B), block_rows(j, a.cam_H[kr], a.B));
-                sw[lane] = fmin(nR, nL) / ((double)a.S * rows);
-                sr[lane] = log(muL) - log(muR);
-                sb[lane] = bpos;
+                w = (double)min(nR, nL) / (double)(a.S * rows);
+                wr = w * log(ratio);
+            } else {
+                bpos = -1;
             }
         }
     }
+    sw[lane] = w;
+    srw[lane] = wr;
+    sb[lane] = bpos;
     __syncwarp();
-    if (lane == 0) {
-        // seams of a chain join members e and e+1; a ring's last seam joins n-1 and 0
-        const bool ring = n >= 2 && sb[n - 1] == 0;
-        const double wc = ring ? sw[n - 1] : 0.0;
-        double rhs[kMaxChain];
-        for (int e = 0; e < n; ++e) rhs[e] = 0.0;
-        for (int e = 0; e < n; ++e) {
-            const int b = sb[e];
-            if (b < 0) continue;
-            rhs[e] += sw[e] * sr[e];
-            rhs[b] -= sw[e] * sr[e];
-        }
-        // Thomas factorisation of T: diag d_k = lambda + w_{k-1} + w_k, off -w_k
-        const double su = 1.0 / sqrt((double)n);
-        const double sv = sqrt(wc);
-        double pb = 0.0, pu = 0.0, pv = 0.0;
-        for (int k = 0; k < n; ++k) {
-            const double wl = (k > 0 && sb[k - 1] == k) ? sw[k - 1] : 0.0;
-            const double wr = (k + 1 < n && sb[k] == k + 1) ? sw[k] : 0.0;
-            const double d = a.lambda + wl + wr;
-            const double den = k == 0 ? d : d - wl * cp[k - 1];      // T_{k,k-1} = -wl
-            const double id = 1.0 / den;
-            cp[k] = -wr * id;                                        // T_{k,k+1} = -wr
-            const double vk = ring ? (k == n - 1 ? sv : (k == 0 ? -sv : 0.0)) : 0.0;
-            pb = (rhs[k] + wl * pb) * id;
-            pu = (su + wl * pu) * id;
-            pv = (vk + wl * pv) * id;
-            zb[k] = pb;
-            zu[k] = pu;
-            zv[k] = pv;
-        }
-        for (int k = n - 2; k >= 0; --k) {
-            zb[k] -= cp[k] * zb[k + 1];
-            zu[k] -= cp[k] * zu[k + 1];
-            zv[k] -= cp[k] * zv[k + 1];
-        }
-        // Woodbury: x = z_b - [z_u z_v] (I + U^T Z)^-1 U^T z_b
-        double uzb = 0.0, uzu = 0.0, uzv = 0.0, vzb = 0.0, vzu = 0.0, vzv = 0.0;
-        for (int k = 0; k < n; ++k) {
-            const double vk = ring ? (k == n - 1 ? sv : (k == 0 ? -sv : 0.0)) : 0.0;
-            uzb += su * zb[k]; uzu += su * zu[k]; uzv += su * zv[k];
-            vzb += vk * zb[k]; vzu += vk * zu[k]; vzv += vk * zv[k];
-        }
-        double c00 = 1.0 + uzu, c01 = uzv, c10 = vzu, c11 = 1.0 + vzv;
-        double alpha_u, alpha_v;
-        if (ring) {
-            const double det = c00 * c11 - c01 * c10;
-            alpha_u = (c11 * uzb - c01 * vzb) / det;
-            alpha_v = (c00 * vzb - c10 * uzb) / det;
-        } else {
-            alpha_u = uzb / c00;
-            alpha_v = 0.0;
-        }
-        for (int k = 0; k < n; ++k) x[k] = zb[k] - zu[k] * alpha_u - zv[k] * alpha_v;
+    // right-hand side, the chain's path weights w_k (seam k, k+1) and the
+    // ring's rank-one vector
+    const bool ring = n >= 2 && sb[n - 1] == 0;
+    const double sv = ring ? sqrt(sw[n - 1]) : 0.0;
+    if (lane < n) {
+        double r = sb[lane] >= 0 ? srw[lane] : 0.0;
+        for (int e = 0; e < n; ++e)
+            if (sb[e] == lane) r -= srw[e];
+        rh[lane] = r;
+        wp[lane] = (lane + 1 < n && sb[lane] == lane + 1) ? sw[lane] : 0.0;
+        vv[lane] = ring ? (lane == n - 1 ? sv : (lane == 0 ? -sv : 0.0)) : 0.0;
     }
     __syncwarp();
+    // 2. forward continuant recurrences (lane 0; one FMA per step each)
+    if (lane == 0) {
+        double Pm2 = 0.0, Pm1 = 1.0, sbm = 0.0, svm = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const double wl = k > 0 ? wp[k - 1] : 0.0;
+            const double d = a.lambda + wl + wp[k];
+            const double pk = fma(d, Pm1, -(wl * wl) * Pm2);
+            sbm = fma(wl, sbm, rh[k] * Pm1);
+            svm = fma(wl, svm, vv[k] * Pm1);
+            P[k] = pk;
+            Pp[k] = Pm1;
+            sB[k] = sbm;
+            sV[k] = svm;
+            Pm2 = Pm1;
+            Pm1 = pk;
+        }
+    }
+    __syncwarp();
+    // 3. the divisions, all lanes at once
     if (lane < n) {
+        const double ip = 1.0 / P[lane];
+        aB[lane] = sB[lane] * ip;
+        aV[lane] = sV[lane] * ip;
+        bt[lane] = wp[lane] * Pp[lane] * ip;
+    }
+    __syncwarp();
+    // 4. backward recurrences (lane 0)
+    if (lane == 0) {
+        double x1 = 0.0, x2 = 0.0;
+        for (int k = n - 1; k >= 0; --k) {
+            x1 = fma(bt[k], x1, aB[k]);
+            x2 = fma(bt[k], x2, aV[k]);
+            xb[k] = x1;
+            xv[k] = x2;
+        }
+    }
+    __syncwarp();
+    // 5. ring: x = x_b - x_v (v^T x_b) / (1 + v^T x_v); gains, smoothing, Q16
+    if (lane < n) {
+        double x = xb[lane];
+        if (ring) {
+            const double vxb = sv * (xb[n - 1] - xb[0]), vxv = sv * (xv[n - 1] - xv[0]);
+            x -= xv[lane] * vxb / (1.0 + vxv);
+        }
         const int cam = a.group_members[g0 + lane];
-        const double g = fmin(fmax(exp(x[lane]), a.gmin), a.gmax);
-        for (int side = 0; side < 2; ++side)
-            smooth_store(a, (((size_t)(cam * 2 + side) * a.B + j) * 3 + c) * 2, g, 0.0);
+        const double g = fmin(fmax(exp(x), a.gmin), a.gmax);
+        const size_t i0 = (((size_t)(cam * 2 + 0) * a.B + j) * 3 + c) * 2;
+        const size_t i1 = (((size_t)(cam * 2 + 1) * a.B + j) * 3 + c) * 2;
+        // both sides carry the same gain: smooth and quantise once, store twice
+        smooth_store(a, i0, g, 0.0);
+        a.maps_new[i1] = a.maps_new[i0];
+        a.maps_new[i1 + 1] = 0.0;
+        a.E[i1] = a.E[i0];
+        a.E[i1 + 1] = a.E[i0 + 1];
+        a.q16[i1] = a.q16[i0];
+        a.q16[i1 + 1] = a.q16[i0 + 1];
     }
 }
 

@@ -17,19 +17,15 @@
 #pragma once
 #include <cstdint>
 
+#include "rt_internal.cuh"
+
 namespace rt {
 
 constexpr uint32_t kMagicBits = 0x4B000000u;   // bits of 2^23
 constexpr float kMagic = 8388608.0f;           // 2^23
 
-struct ConvConsts {
-    float ky;                    // 298 / 65280
-    float krv, c_r0;             // z_R chroma part: V * krv + c_r0
-    float kgu, kgv, c_g0;        // z_G chroma part: U * kgu + V * kgv + c_g0
-    float kbu, c_b0;             // z_B chroma part: U * kbu + c_b0
-};
-
-__host__ __device__ inline ConvConsts conv_consts(int matrix)
+// Host only: the constants travel to the kernels in ArrayGeom::conv.
+inline ConvConsts conv_consts(int matrix)
 {
     // integer coefficients of the standard (round(256 k 255/219 or 255/224))
     const int cy = 298;

@@ -1,15 +1,16 @@
 // Host runtime of librt.so: the C ABI declared in include/rt.h.
 //
 // Pipelining.  Per frame set t the library enqueues
-//   stats stream (high priority):  pass A(t) -> solve(t)          [latency bound, small]
-//   main stream:                   clear(t) -> pass B(t) -> crops(t)  [bandwidth bound]
+//   band stream  (high priority):  pass A(t)                       [small]
+//   solve stream (high priority):  solve(t) after pass A(t)        [latency bound]
+//   main stream:                   clear(t) -> pass B(t) -> crops(t) [bandwidth bound]
 // with pass B(t) waiting for solve(t) (current schedule) or solve(t-1)
-// (lagged schedule).  Pass A / solve of frame set t+1 therefore run while
-// pass B of frame set t streams through HBM, and the latency of the tiny
-// statistics chain hides behind the bandwidth-bound pass.  Buffers written
-// per frame set are double buffered (outputs, histograms, band luma) and the
-// Q16 table is a ring of three; before frame set t reuses a slot the stats
-// stream waits for pass B(t-2) to have finished.
+// (lagged schedule).  Pass A of frame set t+1 overlaps the solve of frame
+// set t, and both overlap pass B of frame set t, so the latency-bound
+// statistics chain hides behind the bandwidth-bound pass.  Outputs,
+// histograms and band luma are double buffered; the band statistics and the
+// Q16 table are rings of three.  Before a slot is reused the stream that
+// writes it waits for the event of its last reader.
 //
 // Every wait the host does is bounded (rt_get_*, rt_sync: cudaEventQuery
 // polling with a deadline), and no kernel waits on another.
@@ -22,6 +23,8 @@
 #include <vector>
 
 #include "rt_internal.cuh"
+#include "pixel.cuh"
+#include "../../include/rt_surrogate.h"
 
 using namespace rt;
 
@@ -35,7 +38,7 @@ constexpr int kMaxProfiled = 4096;  // frame sets whose pass times one collectio
 
 // CUDA events around the passes of one frame set (profiling)
 struct ProfEv {
-    cudaEvent_t a0, a1, s1, b0, b1, c1;
+    cudaEvent_t a0, a1, s0, s1, b0, b1, c1;
     bool crops;
 };
 
@@ -49,7 +52,8 @@ struct rt_handle {
     rt_array_params p{};
     std::vector<rt_camera_desc> cams;
     int dev = 0, sm_count = 0;
-    cudaStream_t user = nullptr, s_stats = nullptr, s_main = nullptr, s_copy = nullptr, s_d2h = nullptr;
+    cudaStream_t user = nullptr, s_stats = nullptr, s_solve = nullptr, s_main = nullptr, s_copy = nullptr,
+                 s_d2h = nullptr;
     ArrayGeom geom{};
     int Hmax = 0;
     // outputs and statistics
@@ -58,9 +62,9 @@ struct rt_handle {
     size_t rgb_bytes = 0;
     uint32_t *frame_hist[2] = {nullptr, nullptr};
     uint32_t *thumbs[2] = {nullptr, nullptr};
-    uint32_t *strip_hist[2] = {nullptr, nullptr};
-    uint32_t *strip_n[2] = {nullptr, nullptr};
-    unsigned long long *strip_sum[2] = {nullptr, nullptr}, *strip_sumsq[2] = {nullptr, nullptr};
+    uint32_t *strip_hist[3] = {nullptr, nullptr, nullptr};
+    uint32_t *strip_n[3] = {nullptr, nullptr, nullptr};
+    unsigned long long *strip_sum[3] = {nullptr, nullptr, nullptr}, *strip_sumsq[3] = {nullptr, nullptr, nullptr};
     uint8_t *luma[2] = {nullptr, nullptr};
     size_t luma_cam_stride = 0;
     double *maps_new = nullptr, *E = nullptr;
@@ -82,7 +86,7 @@ struct rt_handle {
     size_t stage_bytes = 0;
     // events
     cudaEvent_t ev_user = nullptr, ev_in = nullptr, ev_tmp = nullptr;
-    cudaEvent_t ev_solved[kEvRing] = {}, ev_done[kEvRing] = {}, ev_out[kEvRing] = {};
+    cudaEvent_t ev_a[kEvRing] = {}, ev_solved[kEvRing] = {}, ev_done[kEvRing] = {}, ev_out[kEvRing] = {};
     bool launched[kEvRing] = {}, out_launched[kEvRing] = {};
     int64_t t = 0;                 // frame sets submitted
     bool restart = true;           // next submit starts a sequence
@@ -110,6 +114,10 @@ struct rt_handle {
     size_t pb_smem = 0;
     std::string err;
     size_t n_maps = 0;             // K*2*B*3*2
+    // surrogate inference buffers (allocated on first use)
+    void *sg_x = nullptr;          // BF16 [K][6912]
+    float *sg_y = nullptr;         // [K][3]
+    double *sg_maps = nullptr, *sg_err = nullptr;
 };
 
 namespace {
@@ -224,6 +232,10 @@ rt_status validate(const rt_array_params *p)
         units += (unsigned long long)(c.height / 2) * ((c.width + 15) / 16);
     }
     if (units >= (1ull << 31)) return fail(nullptr, RT_ERR_INVALID, "array too large");
+    if (p->flags & RT_FLAG_THUMBNAILS)
+        for (int k = 0; k < p->num_cameras; ++k)
+            if (p->cams[k].width < RT_THUMB_W || p->cams[k].height < RT_THUMB_H)
+                return fail(nullptr, RT_ERR_INVALID, "thumbnails need cameras of at least 64 x 36 pixels");
     return RT_OK;
 }
 
@@ -231,15 +243,17 @@ void free_all(rt_handle *h)
 {
     auto F = [](void *p) { if (p) cudaFree(p); };
     for (int i = 0; i < 2; ++i) {
-        F(h->rgb[i]); F(h->frame_hist[i]); F(h->thumbs[i]); F(h->strip_hist[i]); F(h->strip_sum[i]);
+        F(h->rgb[i]); F(h->frame_hist[i]); F(h->thumbs[i]);
         F(h->luma[i]); F(h->crops[i]); F(h->crop_dev[i]); F(h->stage[i]);
     }
+    for (int i = 0; i < 3; ++i) { F(h->strip_hist[i]); F(h->strip_sum[i]); }
     for (int i = 0; i < kQRing; ++i) F(h->q16[i]);
     F(h->maps_new); F(h->E); F(h->q16_identity); F(h->ramp); F(h->items); F(h->group_start);
     F(h->group_members); F(h->left_nbr); F(h->right_nbr); F(h->cam_H);
     if (h->crop_host) cudaFreeHost(h->crop_host);
-    cudaStream_t ss[] = {h->s_stats, h->s_main, h->s_copy, h->s_d2h};
+    cudaStream_t ss[] = {h->s_stats, h->s_solve, h->s_main, h->s_copy, h->s_d2h};
     for (auto s : ss) if (s) cudaStreamDestroy(s);
+    F(h->sg_x); F(h->sg_y); F(h->sg_maps); F(h->sg_err);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     F(h->cap_crops);
@@ -247,6 +261,7 @@ void free_all(rt_handle *h)
     cudaEvent_t ee[] = {h->ev_user, h->ev_in, h->ev_tmp, h->ev_fork, h->ev_join};
     for (auto e : ee) if (e) cudaEventDestroy(e);
     for (int i = 0; i < kEvRing; ++i) {
+        if (h->ev_a[i]) cudaEventDestroy(h->ev_a[i]);
         if (h->ev_solved[i]) cudaEventDestroy(h->ev_solved[i]);
         if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
         if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
@@ -262,6 +277,7 @@ rt_status setup(rt_handle *h)
     int lo = 0, hi = 0;
     RT_CUDA(h, cudaDeviceGetStreamPriorityRange(&lo, &hi));
     RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_stats, cudaStreamNonBlocking, hi));
+    RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_solve, cudaStreamNonBlocking, hi));
     RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_main, cudaStreamNonBlocking, lo));
     RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking));
     RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_d2h, cudaStreamNonBlocking));
@@ -271,6 +287,7 @@ rt_status setup(rt_handle *h)
     RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     for (int i = 0; i < kEvRing; ++i) {
+        RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_a[i], cudaEventDisableTiming));
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_solved[i], cudaEventDisableTiming));
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming));
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming));
@@ -280,6 +297,7 @@ rt_status setup(rt_handle *h)
     ArrayGeom &g = h->geom;
     memset(&g, 0, sizeof g);
     g.K = K; g.B = B; g.fit_mode = p.fit_mode; g.matrix = p.color_matrix;
+    g.conv = conv_consts(p.color_matrix);
     h->rgb_off.resize(K);
     size_t off = 0;
     uint32_t units = 0;
@@ -299,19 +317,22 @@ rt_status setup(rt_handle *h)
     }
     g.units_total = units;
     h->rgb_bytes = off;
+    for (int i = 0; i < 3; ++i) {
+        rt_status s;
+        // histograms and counts in one allocation, sums and sums of squares in
+        // another, so that pass A clears a slot with two ranges
+        const size_t nb = (size_t)K * 2 * B;
+        if ((s = dalloc(h, &h->strip_hist[i], nb * 768 + nb * 3)) != RT_OK) return s;
+        h->strip_n[i] = h->strip_hist[i] + nb * 768;
+        if ((s = dalloc(h, &h->strip_sum[i], nb * 3 * 2)) != RT_OK) return s;
+        h->strip_sumsq[i] = h->strip_sum[i] + nb * 3;
+    }
     for (int i = 0; i < 2; ++i) {
         rt_status s;
         if ((s = dalloc(h, &h->rgb[i], off)) != RT_OK) return s;
         if ((s = dalloc(h, &h->frame_hist[i], (size_t)K * 768)) != RT_OK) return s;
         if ((p.flags & RT_FLAG_THUMBNAILS) &&
             (s = dalloc(h, &h->thumbs[i], (size_t)K * 3 * RT_THUMB_H * RT_THUMB_W)) != RT_OK) return s;
-        // histograms and counts in one allocation, sums and sums of squares in
-        // another, so that the solve clears a slot with two ranges
-        const size_t nb = (size_t)K * 2 * B;
-        if ((s = dalloc(h, &h->strip_hist[i], nb * 768 + nb * 3)) != RT_OK) return s;
-        h->strip_n[i] = h->strip_hist[i] + nb * 768;
-        if ((s = dalloc(h, &h->strip_sum[i], nb * 3 * 2)) != RT_OK) return s;
-        h->strip_sumsq[i] = h->strip_sum[i] + nb * 3;
         h->luma_cam_stride = (size_t)2 * h->Hmax * S;
         if ((s = dalloc(h, &h->luma[i], (size_t)K * h->luma_cam_stride)) != RT_OK) return s;
         if (p.max_crops > 0) {
@@ -446,6 +467,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     const int K = p.num_cameras;
     const int64_t t = h->t;
     const int par = (int)(t & 1), ev = (int)(t % kEvRing), qs = (int)(t % kQRing);
+    const int ss = (int)(t % 3), ss_next = (int)((t + 1) % 3);   // band-statistics slots
     const bool first = h->restart || frame_index == 0;
 
     ArrayGeom g = h->geom;
@@ -466,14 +488,17 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     }
     const int ev2 = (int)((t + kEvRing - 2) % kEvRing);
     const bool dep2 = h->capturing ? (t - 2 >= h->cap_t0) : (t >= 2 && h->launched[ev2]);
-    if (dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_stats, h->ev_done[ev2], 0));
+    // pass A(t) clears the slot the solve of frame set t-2 read
+    if (dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_stats, h->ev_solved[ev2], 0));
+    // solve(t) overwrites the Q16 slot pass B(t-3) / B(t-2) (lagged) read
+    if (dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_solve, h->ev_done[ev2], 0));
     if (!h->capturing && t >= 2 && h->out_launched[ev2])
         RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_out[ev2], 0));
     ProfEv pe{};
     const bool prof = h->prof_on && (h->capturing || h->prof.size() < (size_t)kMaxProfiled);
     if (prof) {
         rt_status s;
-        cudaEvent_t *evs[] = {&pe.a0, &pe.a1, &pe.s1, &pe.b0, &pe.b1, &pe.c1};
+        cudaEvent_t *evs[] = {&pe.a0, &pe.a1, &pe.s0, &pe.s1, &pe.b0, &pe.b1, &pe.c1};
         for (auto e : evs)
             if ((s = pool_event(h, e)) != RT_OK) return s;
         RT_CUDA(h, prof_record(h, pe.a0, h->s_stats));
@@ -484,23 +509,26 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     pa.first = first ? 1 : 0;
     pa.prev_luma = h->luma[par ^ 1]; pa.cur_luma = h->luma[par];
     pa.luma_cam_stride = (int32_t)h->luma_cam_stride;
-    pa.hist = h->strip_hist[par]; pa.n = h->strip_n[par]; pa.sum = h->strip_sum[par]; pa.sumsq = h->strip_sumsq[par];
+    pa.hist = h->strip_hist[ss]; pa.n = h->strip_n[ss]; pa.sum = h->strip_sum[ss]; pa.sumsq = h->strip_sumsq[ss];
     const size_t nb = (size_t)K * 2 * p.num_blocks;
-    pa.clear_u32 = h->strip_hist[par ^ 1]; pa.clear_u32_n = nb * 768 + nb * 3;
-    pa.clear_u64 = h->strip_sum[par ^ 1]; pa.clear_u64_n = nb * 3 * 2;
+    pa.clear_u32 = h->strip_hist[ss_next]; pa.clear_u32_n = nb * 768 + nb * 3;
+    pa.clear_u64 = h->strip_sum[ss_next]; pa.clear_u64_n = nb * 3 * 2;
     RT_CUDA(h, launch_pass_a(g, pa, 64, h->s_stats));
     if (prof) RT_CUDA(h, prof_record(h, pe.a1, h->s_stats));
+    RT_CUDA(h, cudaEventRecord(h->ev_a[ev], h->s_stats));
+    RT_CUDA(h, cudaStreamWaitEvent(h->s_solve, h->ev_a[ev], 0));
 
     SolveArgs sa{};
-    sa.n = h->strip_n[par]; sa.sum = h->strip_sum[par]; sa.sumsq = h->strip_sumsq[par];
+    sa.n = h->strip_n[ss]; sa.sum = h->strip_sum[ss]; sa.sumsq = h->strip_sumsq[ss];
     sa.maps_new = h->maps_new; sa.E = h->E; sa.q16 = h->q16[qs];
     sa.K = K; sa.B = p.num_blocks; sa.S = p.strip_width; sa.fit_mode = p.fit_mode; sa.min_valid = p.min_valid;
     sa.first = first ? 1 : 0; sa.alpha = p.alpha; sa.lambda = p.lambda; sa.gmin = p.gain_min; sa.gmax = p.gain_max;
     sa.n_groups = h->n_groups; sa.group_start = h->group_start; sa.group_members = h->group_members;
     sa.left_nbr = h->left_nbr; sa.right_nbr = h->right_nbr; sa.cam_H = h->cam_H;
-    RT_CUDA(h, launch_solve(sa, h->s_stats));
-    if (prof) RT_CUDA(h, prof_record(h, pe.s1, h->s_stats));
-    RT_CUDA(h, cudaEventRecord(h->ev_solved[ev], h->s_stats));
+    if (prof) RT_CUDA(h, prof_record(h, pe.s0, h->s_solve));
+    RT_CUDA(h, launch_solve(sa, h->s_solve));
+    if (prof) RT_CUDA(h, prof_record(h, pe.s1, h->s_solve));
+    RT_CUDA(h, cudaEventRecord(h->ev_solved[ev], h->s_solve));
 
     // main chain: clear frame histograms -> pass B -> crops
     const int32_t *q_apply = h->q16[qs];
@@ -518,12 +546,14 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
             q_apply = h->q16[(int)((t + kQRing - 1) % kQRing)];
         }
     }
+    // accumulators of this parity were cleared by pass B of the previous
+    // frame set (or at allocation); this pass B clears the other parity
     uint32_t *fh = (p.flags & RT_FLAG_FRAME_STATS) ? h->frame_hist[par] : nullptr;
-    if (fh) RT_CUDA(h, cudaMemsetAsync(fh, 0, (size_t)K * 768 * 4, h->s_main));
     uint32_t *th = (p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[par] : nullptr;
-    if (th) RT_CUDA(h, cudaMemsetAsync(th, 0, (size_t)K * 3 * RT_THUMB_H * RT_THUMB_W * 4, h->s_main));
     PassBArgs pb{};
     pb.q16 = q_apply; pb.frame_hist = fh; pb.thumbs = th;
+    if (fh) { pb.clear_a = h->frame_hist[par ^ 1]; pb.clear_a_n = (uint32_t)K * 768; }
+    if (th) { pb.clear_b = h->thumbs[par ^ 1]; pb.clear_b_n = (uint32_t)K * 3 * RT_THUMB_H * RT_THUMB_W; }
     if (prof) RT_CUDA(h, prof_record(h, pe.b0, h->s_main));
     RT_CUDA(h, launch_pass_b(g, pb, h->pb_grid, h->pb_threads, h->pb_smem, h->s_main));
     if (prof) RT_CUDA(h, prof_record(h, pe.b1, h->s_main));
@@ -551,6 +581,10 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
         (h->capturing ? h->cap_prof : h->prof).push_back(pe);
     }
     h->n_crops[par] = n_crops;
+    // frame set t is done when its own statistics chain is done too: in the
+    // lagged schedule pass B(t) did not wait for solve(t) (pass B(t+1) needs
+    // it anyway, so this wait costs nothing)
+    if (p.schedule == RT_SCHED_LAGGED) RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_solved[ev], 0));
     RT_CUDA(h, cudaEventRecord(h->ev_done[ev], h->s_main));
     h->launched[ev] = true;
     h->out_launched[ev] = false;
@@ -762,11 +796,11 @@ rt_status rt_get_stats(rt_handle *h, rt_stats_view *out, int32_t timeout_ms)
     if (h->t == 0) return fail(h, RT_ERR_STATE, "no frame set submitted");
     rt_status s = wait_event(h, h->ev_done[last_ev(h)], timeout_ms);
     if (s != RT_OK) return s;
-    const int par = (int)((h->t - 1) & 1);
-    out->strip_hist = h->strip_hist[par];
-    out->strip_n = h->strip_n[par];
-    out->strip_sum = reinterpret_cast<const uint64_t *>(h->strip_sum[par]);
-    out->strip_sumsq = reinterpret_cast<const uint64_t *>(h->strip_sumsq[par]);
+    const int par = (int)((h->t - 1) & 1), ss = (int)((h->t - 1) % 3);
+    out->strip_hist = h->strip_hist[ss];
+    out->strip_n = h->strip_n[ss];
+    out->strip_sum = reinterpret_cast<const uint64_t *>(h->strip_sum[ss]);
+    out->strip_sumsq = reinterpret_cast<const uint64_t *>(h->strip_sumsq[ss]);
     out->frame_hist = (h->p.flags & RT_FLAG_FRAME_STATS) ? h->frame_hist[par] : nullptr;
     out->thumbs = (h->p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[par] : nullptr;
     out->num_cameras = h->p.num_cameras;
@@ -783,6 +817,35 @@ rt_status rt_get_thumb_features(rt_handle *h, void *x_bf16, int32_t timeout_ms)
     rt_status s = wait_event(h, h->ev_done[last_ev(h)], timeout_ms);
     if (s != RT_OK) return s;
     RT_CUDA(h, launch_thumb_features(h->geom, h->thumbs[(int)((h->t - 1) & 1)], x_bf16, h->s_d2h));
+    RT_CUDA(h, cudaEventRecord(h->ev_tmp, h->s_d2h));
+    return wait_event(h, h->ev_tmp, timeout_ms);
+}
+
+rt_status rt_surrogate_predict(rt_handle *h, rt_mlp *m, double *maps_fp64, double *max_error, int32_t timeout_ms)
+{
+    if (!h || !m) return RT_ERR_INVALID;
+    const int K = h->p.num_cameras;
+    if (h->p.fit_mode != RT_FIT_GLOBAL || h->p.num_blocks != 1 || !(h->p.flags & RT_FLAG_THUMBNAILS))
+        return fail(h, RT_ERR_STATE, "the surrogate needs per-camera gains, one block and RT_FLAG_THUMBNAILS");
+    if (h->n_groups * 3 > 96) return fail(h, RT_ERR_INVALID, "at most 32 seam chains");
+    if (h->t == 0) return fail(h, RT_ERR_STATE, "no frame set submitted");
+    rt_status s;
+    if (!h->sg_x) {
+        if ((s = dalloc(h, reinterpret_cast<uint16_t **>(&h->sg_x), (size_t)K * 6912)) != RT_OK) return s;
+        if ((s = dalloc(h, &h->sg_y, (size_t)K * 3)) != RT_OK) return s;
+        if ((s = dalloc(h, &h->sg_maps, h->n_maps)) != RT_OK) return s;
+        if ((s = dalloc(h, &h->sg_err, 1)) != RT_OK) return s;
+    }
+    if ((s = rt_get_thumb_features(h, h->sg_x, timeout_ms)) != RT_OK) return s;
+    for (int k0 = 0; k0 < K; k0 += 256) {
+        const int n = K - k0 < 256 ? K - k0 : 256;
+        s = rt_mlp_forward(m, static_cast<uint16_t *>(h->sg_x) + (size_t)k0 * 6912, n, h->sg_y + k0 * 3);
+        if (s != RT_OK) return fail(h, s, std::string("surrogate network: ") + rt_mlp_last_error(m));
+    }
+    RT_CUDA(h, launch_surrogate_gains(h->sg_y, h->group_start, h->group_members, h->n_groups, h->maps_new,
+                                      h->p.gain_min, h->p.gain_max, h->sg_maps, h->sg_err, h->s_d2h));
+    if (maps_fp64) RT_CUDA(h, cudaMemcpyAsync(maps_fp64, h->sg_maps, h->n_maps * 8, cudaMemcpyDefault, h->s_d2h));
+    if (max_error) RT_CUDA(h, cudaMemcpyAsync(max_error, h->sg_err, 8, cudaMemcpyDefault, h->s_d2h));
     RT_CUDA(h, cudaEventRecord(h->ev_tmp, h->s_d2h));
     return wait_event(h, h->ev_tmp, timeout_ms);
 }
@@ -855,6 +918,7 @@ rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y
     rt_status st = RT_OK;
     cudaError_t e = cudaEventRecord(h->ev_fork, h->s_main);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_stats, h->ev_fork, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_solve, h->ev_fork, 0);
     if (e != cudaSuccess) st = cuda_fail(h, e, "fork");
     for (int i = 0; i < n_sets && st == RT_OK; ++i) {
         const int nc = n_crops ? n_crops[i] : 0;
@@ -864,6 +928,8 @@ rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y
     }
     if (st == RT_OK) {
         e = cudaEventRecord(h->ev_join, h->s_stats);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_main, h->ev_join, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->s_solve);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_main, h->ev_join, 0);
         if (e != cudaSuccess) st = cuda_fail(h, e, "join");
     }
@@ -897,6 +963,8 @@ rt_status rt_launch_sequence(rt_handle *h)
     // earlier frame sets' statistics chain and copies finish before the graph starts
     RT_CUDA(h, cudaEventRecord(h->ev_tmp, h->s_stats));
     RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_tmp, 0));
+    RT_CUDA(h, cudaEventRecord(h->ev_tmp, h->s_solve));
+    RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_tmp, 0));
     RT_CUDA(h, cudaEventRecord(h->ev_tmp, h->s_d2h));
     RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_tmp, 0));
     RT_CUDA(h, cudaGraphLaunch(h->graph_exec, h->s_main));
@@ -907,6 +975,7 @@ rt_status rt_launch_sequence(rt_handle *h)
     // events last recorded inside the capture are re-recorded after the graph
     // so that later single submits can wait on them
     for (int i = 0; i < kEvRing; ++i) {
+        RT_CUDA(h, cudaEventRecord(h->ev_a[i], h->s_main));
         RT_CUDA(h, cudaEventRecord(h->ev_solved[i], h->s_main));
         if (i != ev) RT_CUDA(h, cudaEventRecord(h->ev_done[i], h->s_main));
         h->launched[i] = true;
@@ -927,7 +996,7 @@ rt_status rt_profile(rt_handle *h, int32_t enable)
         if (s != RT_OK) return s;
         h->prof.clear();
         // events captured into a graph keep their pool slots
-        h->ev_pool_used = h->cap_prof.size() * 6;
+        h->ev_pool_used = h->cap_prof.size() * 7;
         if (h->cap_prof.empty()) h->ev_pool_used = 0;
     }
     h->prof_on = enable != 0;
@@ -946,7 +1015,7 @@ rt_status rt_get_profile(rt_handle *h, rt_profile_report *out, int32_t timeout_m
     for (const ProfEv &pe : v) {
         float a = 0, b = 0, c = 0, d = 0;
         RT_CUDA(h, cudaEventElapsedTime(&a, pe.a0, pe.a1));
-        RT_CUDA(h, cudaEventElapsedTime(&b, pe.a1, pe.s1));
+        RT_CUDA(h, cudaEventElapsedTime(&b, pe.s0, pe.s1));
         RT_CUDA(h, cudaEventElapsedTime(&c, pe.b0, pe.b1));
         if (pe.crops) RT_CUDA(h, cudaEventElapsedTime(&d, pe.b1, pe.c1));
         out->pass_a_ms += a;
@@ -961,7 +1030,7 @@ rt_status rt_get_profile(rt_handle *h, rt_profile_report *out, int32_t timeout_m
 rt_status rt_sync(rt_handle *h, int32_t timeout_ms)
 {
     if (!h) return RT_ERR_INVALID;
-    cudaStream_t ss[] = {h->s_copy, h->s_stats, h->s_main, h->s_d2h};
+    cudaStream_t ss[] = {h->s_copy, h->s_stats, h->s_solve, h->s_main, h->s_d2h};
     for (auto st : ss) {
         RT_CUDA(h, cudaEventRecord(h->ev_tmp, st));
         rt_status s = wait_event(h, h->ev_tmp, timeout_ms);

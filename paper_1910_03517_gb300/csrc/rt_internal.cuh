@@ -25,8 +25,18 @@ struct CamGeom {
     const int32_t *ramp;    // Q16 ramp weight per column (seam maps)
 };
 
+// Colour-conversion constants (see pixel.cuh), computed on the host: the
+// GB300's FP64 pipe is narrow, so device code never derives them itself.
+struct ConvConsts {
+    float ky;                    // 298 / 65280
+    float krv, c_r0;             // z_R chroma part: V * krv + c_r0
+    float kgu, kgv, c_g0;        // z_G chroma part: U * kgu + V * kgv + c_g0
+    float kbu, c_b0;             // z_B chroma part: U * kbu + c_b0
+};
+
 struct ArrayGeom {
     CamGeom cam[RT_MAX_CAMERAS];
+    ConvConsts conv;
     int32_t K, B, fit_mode, matrix;
     uint32_t units_total;   // sum over cameras of (H/2) * upr
 };
@@ -36,6 +46,9 @@ struct PassBArgs {
     const int32_t *q16;       // [K][2][B][3][2]
     uint32_t *frame_hist;     // [K][3][256] (nullptr: statistics off)
     uint32_t *thumbs;         // [K][3][36][64] (nullptr: off)
+    // the next frame set's accumulators (the other parity), cleared here
+    uint32_t *clear_a; uint32_t clear_a_n;
+    uint32_t *clear_b; uint32_t clear_b_n;
 };
 
 // Pass A work item: one camera side, rows [row0, row1) all inside block j.
@@ -88,5 +101,8 @@ cudaError_t launch_pass_a(const ArrayGeom &g, const PassAArgs &a, int threads, c
 cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_crops(const ArrayGeom &g, const CropArgs &a, cudaStream_t s);
 cudaError_t launch_thumb_features(const ArrayGeom &g, const uint32_t *thumbs, void *out, cudaStream_t s);
+cudaError_t launch_surrogate_gains(const float *y, const int32_t *group_start, const int32_t *group_members,
+                                   int n_groups, const double *maps_fit, double gmin, double gmax, double *maps_out,
+                                   double *err_out, cudaStream_t s);
 
 }  // namespace rt

@@ -288,6 +288,15 @@ class CameraArray:
         return {"frame_sets": r.frame_sets, "pass_a_ms": r.pass_a_ms, "solve_ms": r.solve_ms,
                 "pass_b_ms": r.pass_b_ms, "crops_ms": r.crops_ms}
 
+    def surrogate_predict(self, net: "GainMLP", timeout_ms: int = 60000):
+        """(maps [K,2,1,3,2] predicted by the network, judge error vs the fit)."""
+        _load_mlp(self.L)
+        maps = np.zeros((self.K, 2, self.B, 3, 2), np.float64)
+        err = np.zeros(1, np.float64)
+        _check(self.L, self.h, self.L.rt_surrogate_predict(self.h, net.h, maps.ctypes.data, err.ctypes.data,
+                                                           timeout_ms))
+        return maps, float(err[0])
+
     def thumb_features(self, timeout_ms: int = 60000):
         """BF16 device tensor [K, 6912] of the last frame set's thumbnail features."""
         import torch
@@ -328,7 +337,7 @@ class CameraArray:
 MLP_INPUTS = 6912
 MLP_PARAMS = 1836291
 MLP_EXPORTS = ["rt_mlp_create", "rt_mlp_set_params", "rt_mlp_get_params", "rt_mlp_forward", "rt_mlp_gradients",
-               "rt_mlp_train_step", "rt_mlp_last_error", "rt_mlp_destroy"]
+               "rt_mlp_train_step", "rt_mlp_last_error", "rt_mlp_destroy", "rt_surrogate_predict"]
 
 
 def _load_mlp(L):
@@ -344,7 +353,9 @@ def _load_mlp(L):
     L.rt_mlp_last_error.restype = ctypes.c_char_p
     L.rt_mlp_destroy.argtypes = [c_vp]
     L.rt_mlp_destroy.restype = None
-    for n in MLP_EXPORTS[:-2]:
+    L.rt_surrogate_predict.argtypes = [c_vp, c_vp, c_vp, c_vp, c_i32]
+    L.rt_surrogate_predict.restype = c_i32
+    for n in MLP_EXPORTS[:-3]:
         getattr(L, n).restype = c_i32
     L._mlp_ready = True
 

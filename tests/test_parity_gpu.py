@@ -294,7 +294,7 @@ def test_thumbnails_and_features(rt, orc):
     run_sequence(rt, orc, synth.small_pair(), 2, thumbs=True)
     cams = [synth.Camera(72, 38, position=0, y_pitch=80, uv_pitch=80),
             synth.Camera(130, 76, position=1, y_pitch=144, uv_pitch=144),
-            synth.Camera(90, 20, fmt=synth.MONO16, bit_depth=12, group=1, y_pitch=192)]
+            synth.Camera(90, 40, fmt=synth.MONO16, bit_depth=12, group=1, y_pitch=192)]
     wl = synth.Workload("ragged thumbs", cams, frames=2, seed=21)
     run_sequence(rt, orc, wl, 2, thumbs=True, strip_width=16, min_valid=8)
     run_sequence(rt, orc, synth.tower12(frames=1), 1, thumbs=True, stats=False)

@@ -1,12 +1,22 @@
 """GPU parity of the learned gain surrogate's tensor-core kernels against the
 FP64 oracle (oracle/mlp.py) on identical BF16 operands.
 
-Bars: forward outputs and every parameter gradient within 1e-3 of the
-oracle relative to the tensor's norm; the batch loss within 1e-3 relative.
-The GPU accumulates in FP32 and stores hidden activations and their
-gradients in BF16; the oracle rounds at the same points and accumulates the
-sums it rounds in float32 (acc32), so that both sides take each BF16
-rounding decision in the kernel's precision.
+Primary pin (bit-exact): on sparse dyadic inputs every sum of the forward
+and backward pass is exactly representable in FP32, which the test proves
+by checking that the oracle's float32 and float64 paths agree bit for bit;
+there any correct implementation must reproduce the oracle's output, loss
+and every gradient exactly, whatever order it adds in.
+
+Random inputs (statistical): the tensor cores do not add like a sequential
+IEEE FP32 loop, so on random data the GPU differs from the FP32-accumulating
+oracle by ~4e-4 relative in the forward (measured on GB300), and BF16
+rounding decisions of activations and ReLU masks amplify that in the
+gradients of earlier layers (measured up to ~1.5e-2 relative to the norm
+for W1 at batch 96).
+
+Bars on random inputs: forward outputs within 1e-3 of the oracle relative
+to the output's norm; the batch loss within 1e-3 relative; gradients within
+3e-2 relative to each tensor's norm and correlated above 0.999.
 """
 import numpy as np
 import pytest
@@ -78,7 +88,51 @@ def test_gradients_match_oracle(rt, n):
     assert abs(loss - omlp.mse(y, t)) <= 1e-3 * omlp.mse(y, t)
     gd = _flat_to_dict(rt, g)
     errs = {name: _rel(gd[name], G[name]) for name in G}
-    assert max(errs.values()) < 1e-3, errs
+    corr = {name: float(np.corrcoef(gd[name].ravel(), G[name].ravel())[0, 1]) for name in G if G[name].size > 3}
+    assert max(errs.values()) < 3e-2, errs
+    assert min(corr.values()) > 0.999, corr
+
+
+def _exact_case(rt, n, seed):
+    """Sparse dyadic parameters and inputs whose every sum is exact in FP32."""
+    rng = np.random.default_rng(seed)
+    flat = np.zeros(rt.MLP_PARAMS, np.float32)
+    for name, off, shape in rt.param_offsets():
+        m = int(np.prod(shape))
+        if len(shape) == 2:
+            v = rng.choice([-1.0, 0.0, 1.0], size=m, p=[0.25, 0.5, 0.25]) / 16.0
+        else:
+            v = rng.integers(-2, 3, size=m) / 256.0
+        flat[off:off + m] = v
+    x = (rng.choice([-1.0, 0.0, 1.0], size=(n, omlp.D_IN), p=[0.03, 0.94, 0.03]) / 16.0).astype(np.float32)
+    return flat, x
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_forward_and_gradients_bit_exact_on_exact_arithmetic(rt, n):
+    flat, x = _exact_case(rt, n, 100 + n)
+    P = _flat_to_dict(rt, flat)
+    y32, c32 = omlp.forward(P, x.astype(np.float64), bf16=True, acc32=True)
+    y64, c64 = omlp.forward(P, x.astype(np.float64), bf16=True, acc32=False)
+    assert np.array_equal(y32, y64)                      # the forward sums are exact
+    # targets that make dy = 2 (y - t) / (3 n) a small dyadic number
+    k = np.random.default_rng(n).integers(-2, 3, size=(n, 3))
+    t = (y64 - 3 * n * k * 2.0 ** -14).astype(np.float32)
+    assert np.array_equal(t.astype(np.float64), y64 - 3 * n * k * 2.0 ** -14)
+    G32 = omlp.backward(P, c32, t.astype(np.float64), bf16=True, acc32=True)
+    G64 = omlp.backward(P, c64, t.astype(np.float64), bf16=True, acc32=False)
+    for name in G64:
+        assert np.array_equal(G32[name], G64[name]), name   # the backward sums are exact too
+    net = rt.GainMLP()
+    net.set_params(flat)
+    xt = torch.from_numpy(x).to(torch.bfloat16).cuda()
+    y = net.forward(xt).cpu().numpy().astype(np.float64)
+    assert np.array_equal(y, y64)
+    g, loss = net.gradients(xt, torch.from_numpy(t).cuda())
+    gd = _flat_to_dict(rt, g)
+    for name in G64:
+        assert np.array_equal(gd[name], G64[name]), (name, np.abs(gd[name] - G64[name]).max())
+    net.close()
     net.close()
 
 
@@ -94,11 +148,16 @@ def test_adam_step_matches_oracle(rt):
     G = omlp.backward(P, cache, t.astype(np.float64), bf16=True, acc32=True)
     ref = omlp.adam_step(dict(P), G, {}, lr=1e-3, t=1)
     got = _flat_to_dict(rt, after)
+    # Adam's first step is -lr * g / (|g| + eps): -lr * sign(g) wherever |g| >> eps.
+    # Where the oracle's gradient is clearly away from zero the step must be that
+    # (a few sign flips of near-zero entries are gradient noise, not Adam's)
     for name in P:
         step_ref = ref[name] - P[name]
         step_got = got[name] - P[name]
-        # the first Adam step is lr * sign(g) except where |g| is tiny: compare the step
-        assert _rel(step_got, step_ref) < 2e-2, name
+        assert np.abs(step_got).max() <= 1e-3 * (1 + 1e-5), name
+        big = np.abs(G[name]) > 1e-2 * np.abs(G[name]).max()
+        ok = np.abs(step_got[big] - step_ref[big]) <= 2e-2 * 1e-3
+        assert ok.mean() > 0.99, (name, ok.mean())
     net.close()
 
 
@@ -114,3 +173,40 @@ def test_training_fits_a_linear_teacher(rt):
         losses.append(net.train_step(torch.from_numpy(x).to(torch.bfloat16).cuda(), torch.from_numpy(t).cuda(), 1e-3))
     assert np.mean(losses[-10:]) < 0.2 * np.mean(losses[:3]), (losses[:3], losses[-10:])
     net.close()
+
+
+def test_trained_surrogate_beats_no_correction(rt):
+    """Train on arrays labelled by the per-camera gain fit, then predict the
+    gains of unseen arrays: the re-gauged prediction error must be well below
+    the error of leaving the cameras uncorrected (identity gains)."""
+    from paper_1910_03517_gb300 import surrogate as sg
+    Xtr, Ytr = sg.make_dataset(160, seed=1, n_cams=16, width=256, height=144)
+    Xte, Yte = sg.make_dataset(24, seed=2, n_cams=16, width=256, height=144)
+    net = rt.GainMLP()
+    net.set_params(sg.init_params(0))
+    losses = sg.train(net, Xtr, Ytr, epochs=6, lr=1e-3)
+    assert np.mean(losses[-5:]) < 0.5 * np.mean(losses[:5])
+    pred = sg.regauge(sg.predict(net, Xte), 16)
+    lab = Yte.cpu().numpy()
+    err = sg.gain_error(pred, lab)
+    err_id = sg.gain_error(np.zeros_like(lab), lab)
+    assert np.median(err) < 0.5 * np.median(err_id), (np.median(err), np.median(err_id))
+    # inference + judge through the handle: re-gauged clamped gains and the
+    # largest relative deviation from the fit of the same frame set
+    wl = sg.training_workload(16, 256, 144, seed=77)
+    arr = rt.CameraArray(wl.cams, flags=rt.RT_FLAG_THUMBNAILS)
+    arr.submit_frames(synth_frames(wl), 0)
+    fit, _ = arr.get_gains()
+    pmaps, perr = arr.surrogate_predict(net)
+    y = net.forward(arr.thumb_features()).cpu().numpy().astype(np.float64)
+    want = np.clip(np.exp(y - y.mean(0, keepdims=True)), 0.25, 4.0)
+    assert np.abs(pmaps[:, 0, 0, :, 0] - want).max() < 1e-9
+    assert (pmaps[:, 1] == pmaps[:, 0]).all() and (pmaps[..., 1] == 0).all()
+    assert abs(perr - np.abs(want / fit[:, 0, 0, :, 0] - 1).max()) < 1e-9
+    arr.close()
+    net.close()
+
+
+def synth_frames(wl):
+    from paper_1910_03517_gb300 import synth
+    return synth.frame_set(wl, 0, device="cuda")
