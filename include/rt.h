@@ -255,6 +255,33 @@ rt_status rt_sync(rt_handle *h, int32_t timeout_ms);
 rt_status rt_save_state(rt_handle *h, void *buf, size_t *len);
 rt_status rt_load_state(rt_handle *h, const void *buf, size_t len);
 
+/* Per-camera gains of ONE frame set without allocating anything.  No
+ * counterpart in the paper: this is for callers that cannot call cudaMalloc
+ * -- code that runs inside another framework's memory pool or allocator,
+ * in a process whose device memory is reserved up front, or in a plug-in
+ * that must not grow the device footprint -- and so cannot create a handle
+ * (rt_array_config allocates its buffers).  It runs the band statistics and
+ * the FP64 per-camera gain fit of the handle path's first frame set of a
+ * sequence (no motion test, no smoothing history; defaults of
+ * rt_default_params otherwise, BT.709, per-camera gains) and writes
+ *   maps_dev  doubles [K][2][B][3][2] = (g, 0), as rt_get_gains;
+ *   q16_dev   int32   [K][2][B][3][2] = round(65536 g), round(65536 * 0),
+ * both DEVICE memory owned by the caller; the planes are device pointers
+ * laid out as for rt_submit_frames.  All work is enqueued on cuda_stream
+ * (cudaStream_t) and the call returns without waiting.
+ * Limits (RT_ERR_INVALID beyond them): at most 16 cameras, 4 blocks, a band
+ * width of 16 or 32, 2160 rows per camera.  Its working memory is one
+ * 2.7 MB array inside librt.so that every GPU which loads the library holds
+ * until the process exits.  The first call on a device looks up that
+ * array's device address (make it before any stream capture on the device).
+ * Every call uses the same array: calls whose work overlaps on the GPU race
+ * with each other; the array keeps the last call's contents, and the
+ * statistics part is cleared at the start of every call. */
+rt_status rt_fit_gains_noalloc(const rt_camera_desc *cams, int32_t num_cameras,
+                               const void *const *y_planes, const void *const *uv_planes,
+                               int32_t strip_width, int32_t num_blocks, int32_t topology,
+                               double *maps_dev, int32_t *q16_dev, void *cuda_stream);
+
 /* Text of the last error on this handle (or of the last failed
  * rt_array_config when h is NULL).  Valid until the next call. */
 const char *rt_last_error(rt_handle *h);
