@@ -233,11 +233,17 @@ rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y
  * submitted in between broke the ring's slot alignment (a multiple of 6). */
 rt_status rt_launch_sequence(rt_handle *h);
 
-/* Per-pass device times, from CUDA events the library records around each
- * of its kernels when profiling is on.  rt_profile(h, 1) starts collecting
- * (and clears what was collected), rt_profile(h, 0) stops.  rt_get_profile
- * waits (bounded) and reports totals over the frame sets collected: for a
- * captured sequence, the frame sets of its last launch. */
+/* Per-pass device times, from CUDA events the library records around its
+ * kernels when profiling is on.  rt_profile(h, RT_PROFILE_ALL) starts
+ * collecting around every pass, rt_profile(h, RT_PROFILE_PASS_B) around the
+ * correction pass only (the other totals stay 0; two events per frame set
+ * instead of seven, so the timing disturbs a captured sequence less); both
+ * clear what was collected.  rt_profile(h, 0) stops.  rt_get_profile waits
+ * (bounded) and reports totals over the frame sets collected: for a captured
+ * sequence, the frame sets of its last launch, with the mode in force at
+ * capture. */
+#define RT_PROFILE_ALL 1
+#define RT_PROFILE_PASS_B 2
 typedef struct {
     int32_t frame_sets;
     double pass_a_ms, solve_ms, pass_b_ms, crops_ms;   /* totals, milliseconds */

@@ -39,7 +39,7 @@ constexpr int kMaxProfiled = 4096;  // frame sets whose pass times one collectio
 // CUDA events around the passes of one frame set (profiling)
 struct ProfEv {
     cudaEvent_t a0, a1, s0, s1, b0, b1, c1;
-    bool crops;
+    bool crops, all;
 };
 
 thread_local std::string g_config_error;
@@ -54,6 +54,7 @@ struct rt_handle {
     int dev = 0, sm_count = 0;
     cudaStream_t user = nullptr, s_stats = nullptr, s_solve = nullptr, s_main = nullptr, s_copy = nullptr,
                  s_d2h = nullptr;
+    cudaStream_t s_prof[3] = {nullptr, nullptr, nullptr};   // timing branches of s_stats, s_solve, s_main
     ArrayGeom geom{};
     int Hmax = 0;
     // outputs and statistics
@@ -92,7 +93,7 @@ struct rt_handle {
     bool restart = true;           // next submit starts a sequence
     bool last_first = true;        // the last frame set started its sequence
     // profiling
-    bool prof_on = false;
+    bool prof_on = false, prof_all = true;
     std::vector<ProfEv> prof, cap_prof;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_pool_used = 0;
@@ -106,7 +107,8 @@ struct rt_handle {
     bool capturing = false;
     rt_crop *cap_crops = nullptr;
     size_t cap_crops_n = 0;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_mark = nullptr;
+    bool prof_branch[3] = {false, false, false};   // the capture in progress used s_prof[i]
     // pass B launch shape
     // one pass-B CTA per SM: 896 x 64 registers leave room for pass A and the
     // solve of the next frame set to run beside it
@@ -251,14 +253,15 @@ void free_all(rt_handle *h)
     F(h->maps_new); F(h->E); F(h->q16_identity); F(h->ramp); F(h->items); F(h->group_start);
     F(h->group_members); F(h->left_nbr); F(h->right_nbr); F(h->cam_H);
     if (h->crop_host) cudaFreeHost(h->crop_host);
-    cudaStream_t ss[] = {h->s_stats, h->s_solve, h->s_main, h->s_copy, h->s_d2h};
+    cudaStream_t ss[] = {h->s_stats, h->s_solve, h->s_main, h->s_copy, h->s_d2h,
+                         h->s_prof[0], h->s_prof[1], h->s_prof[2]};
     for (auto s : ss) if (s) cudaStreamDestroy(s);
     F(h->sg_x); F(h->sg_y); F(h->sg_maps); F(h->sg_err);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     F(h->cap_crops);
     for (auto e : h->ev_pool) cudaEventDestroy(e);
-    cudaEvent_t ee[] = {h->ev_user, h->ev_in, h->ev_tmp, h->ev_fork, h->ev_join};
+    cudaEvent_t ee[] = {h->ev_user, h->ev_in, h->ev_tmp, h->ev_fork, h->ev_join, h->ev_mark};
     for (auto e : ee) if (e) cudaEventDestroy(e);
     for (int i = 0; i < kEvRing; ++i) {
         if (h->ev_a[i]) cudaEventDestroy(h->ev_a[i]);
@@ -280,12 +283,14 @@ rt_status setup(rt_handle *h)
     RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_solve, cudaStreamNonBlocking, hi));
     RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_main, cudaStreamNonBlocking, lo));
     RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking));
+    for (int i = 0; i < 3; ++i) RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_prof[i], cudaStreamNonBlocking));
     RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_d2h, cudaStreamNonBlocking));
     RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_user, cudaEventDisableTiming));
     RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
     RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_tmp, cudaEventDisableTiming));
     RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_mark, cudaEventDisableTiming));
     for (int i = 0; i < kEvRing; ++i) {
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_a[i], cudaEventDisableTiming));
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_solved[i], cudaEventDisableTiming));
@@ -448,12 +453,23 @@ rt_status pool_event(rt_handle *h, cudaEvent_t *e)
     return RT_OK;
 }
 
-// Timing event of the profiler: inside a capture it must become an event
+// Timing event of the profiler.  Inside a capture it must become an event
 // record node of the graph (an ordinary record there only expresses a
-// dependency between the captured streams).
+// dependency between the captured streams), and such a node on the critical
+// path delays every later kernel of the graph by microseconds.  So the node
+// goes on a side branch (one stream s_prof[i] per timed stream, so that
+// the branches do not order the streams' marks among each other) that
+// depends on what precedes the timed point on st while nothing on st
+// depends on it; the branches join the main stream at the end of the capture.
 cudaError_t prof_record(rt_handle *h, cudaEvent_t e, cudaStream_t st)
 {
-    return h->capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
+    if (!h->capturing) return cudaEventRecord(e, st);
+    const int i = st == h->s_stats ? 0 : (st == h->s_solve ? 1 : 2);
+    cudaError_t r = cudaEventRecord(h->ev_mark, st);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(h->s_prof[i], h->ev_mark, 0);
+    if (r == cudaSuccess) r = cudaEventRecordWithFlags(e, h->s_prof[i], cudaEventRecordExternal);
+    if (r == cudaSuccess) h->prof_branch[i] = true;
+    return r;
 }
 
 // Enqueue one frame set whose planes are device addresses in y[] / uv[].
@@ -496,12 +512,14 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
         RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_out[ev2], 0));
     ProfEv pe{};
     const bool prof = h->prof_on && (h->capturing || h->prof.size() < (size_t)kMaxProfiled);
+    const bool prof_chain = prof && h->prof_all;   // events around pass A and the solve too
     if (prof) {
         rt_status s;
         cudaEvent_t *evs[] = {&pe.a0, &pe.a1, &pe.s0, &pe.s1, &pe.b0, &pe.b1, &pe.c1};
         for (auto e : evs)
             if ((s = pool_event(h, e)) != RT_OK) return s;
-        RT_CUDA(h, prof_record(h, pe.a0, h->s_stats));
+        pe.all = prof_chain;
+        if (prof_chain) RT_CUDA(h, prof_record(h, pe.a0, h->s_stats));
     }
     // statistics chain: pass A -> solve
     PassAArgs pa{};
@@ -514,7 +532,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     pa.clear_u32 = h->strip_hist[ss_next]; pa.clear_u32_n = nb * 768 + nb * 3;
     pa.clear_u64 = h->strip_sum[ss_next]; pa.clear_u64_n = nb * 3 * 2;
     RT_CUDA(h, launch_pass_a(g, pa, 64, h->s_stats));
-    if (prof) RT_CUDA(h, prof_record(h, pe.a1, h->s_stats));
+    if (prof_chain) RT_CUDA(h, prof_record(h, pe.a1, h->s_stats));
     RT_CUDA(h, cudaEventRecord(h->ev_a[ev], h->s_stats));
     RT_CUDA(h, cudaStreamWaitEvent(h->s_solve, h->ev_a[ev], 0));
 
@@ -525,9 +543,9 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     sa.first = first ? 1 : 0; sa.alpha = p.alpha; sa.lambda = p.lambda; sa.gmin = p.gain_min; sa.gmax = p.gain_max;
     sa.n_groups = h->n_groups; sa.group_start = h->group_start; sa.group_members = h->group_members;
     sa.left_nbr = h->left_nbr; sa.right_nbr = h->right_nbr; sa.cam_H = h->cam_H;
-    if (prof) RT_CUDA(h, prof_record(h, pe.s0, h->s_solve));
+    if (prof_chain) RT_CUDA(h, prof_record(h, pe.s0, h->s_solve));
     RT_CUDA(h, launch_solve(sa, h->s_solve));
-    if (prof) RT_CUDA(h, prof_record(h, pe.s1, h->s_solve));
+    if (prof_chain) RT_CUDA(h, prof_record(h, pe.s1, h->s_solve));
     RT_CUDA(h, cudaEventRecord(h->ev_solved[ev], h->s_solve));
 
     // main chain: clear frame histograms -> pass B -> crops
@@ -913,6 +931,7 @@ rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y
     h->cap_prof.clear();
     h->graph_launched = false;
     h->capturing = true;
+    for (int i = 0; i < 3; ++i) h->prof_branch[i] = false;
     h->cap_t0 = t0;
     RT_CUDA(h, cudaStreamBeginCapture(h->s_main, cudaStreamCaptureModeThreadLocal));
     rt_status st = RT_OK;
@@ -931,6 +950,11 @@ rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_main, h->ev_join, 0);
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->s_solve);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_main, h->ev_join, 0);
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+            if (!h->prof_branch[i]) continue;
+            e = cudaEventRecord(h->ev_join, h->s_prof[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_main, h->ev_join, 0);
+        }
         if (e != cudaSuccess) st = cuda_fail(h, e, "join");
     }
     cudaGraph_t graph = nullptr;
@@ -991,7 +1015,10 @@ rt_status rt_launch_sequence(rt_handle *h)
 rt_status rt_profile(rt_handle *h, int32_t enable)
 {
     if (!h) return RT_ERR_INVALID;
+    if (enable != 0 && enable != RT_PROFILE_ALL && enable != RT_PROFILE_PASS_B)
+        return fail(h, RT_ERR_INVALID, "unknown profiling mode");
     if (enable) {
+        h->prof_all = enable == RT_PROFILE_ALL;
         rt_status s = rt_sync(h, -1);
         if (s != RT_OK) return s;
         h->prof.clear();
@@ -1014,8 +1041,10 @@ rt_status rt_get_profile(rt_handle *h, rt_profile_report *out, int32_t timeout_m
     const std::vector<ProfEv> &v = (h->graph_launched && !h->cap_prof.empty()) ? h->cap_prof : h->prof;
     for (const ProfEv &pe : v) {
         float a = 0, b = 0, c = 0, d = 0;
-        RT_CUDA(h, cudaEventElapsedTime(&a, pe.a0, pe.a1));
-        RT_CUDA(h, cudaEventElapsedTime(&b, pe.s0, pe.s1));
+        if (pe.all) {
+            RT_CUDA(h, cudaEventElapsedTime(&a, pe.a0, pe.a1));
+            RT_CUDA(h, cudaEventElapsedTime(&b, pe.s0, pe.s1));
+        }
         RT_CUDA(h, cudaEventElapsedTime(&c, pe.b0, pe.b1));
         if (pe.crops) RT_CUDA(h, cudaEventElapsedTime(&d, pe.b1, pe.c1));
         out->pass_a_ms += a;

@@ -23,6 +23,8 @@ RT_SCHED_CURRENT, RT_SCHED_LAGGED = 0, 1
 RT_BT709, RT_BT601 = 0, 1
 RT_FLAG_FRAME_STATS = 1
 RT_FLAG_THUMBNAILS = 2
+RT_PROFILE_ALL = 1
+RT_PROFILE_PASS_B = 2
 RT_MAX_CAMERAS = 32
 
 # every symbol include/rt.h declares (checked by the tests)
@@ -279,8 +281,10 @@ class CameraArray:
     def launch_sequence(self):
         _check(self.L, self.h, self.L.rt_launch_sequence(self.h))
 
-    def profile(self, enable: bool):
-        _check(self.L, self.h, self.L.rt_profile(self.h, 1 if enable else 0))
+    def profile(self, enable, pass_b_only: bool = False):
+        """Start (enable true: clears what was collected) or stop collecting."""
+        mode = (RT_PROFILE_PASS_B if pass_b_only else RT_PROFILE_ALL) if enable else 0
+        _check(self.L, self.h, self.L.rt_profile(self.h, mode))
 
     def get_profile(self, timeout_ms: int = 60000) -> Dict[str, float]:
         r = ProfileReport()

@@ -286,6 +286,17 @@ def test_captured_ring_matches_single_submits(rt, kw):
     with pytest.raises(rt.RtError) as ei:
         a.launch_sequence()
     assert ei.value.status == rt.RT_ERR_STATE
+    # events around pass B only: the other passes report nothing
+    a.profile(True, pass_b_only=True)
+    order = [(14 + j) % ring for j in range(ring)]
+    a.capture_sequence([frames[i] for i in order], [crops[i] for i in order])
+    a.profile(False)
+    a.launch_sequence()
+    prof = a.get_profile()
+    assert prof["frame_sets"] == ring
+    assert prof["pass_b_ms"] > 0 and prof["crops_ms"] > 0
+    assert prof["pass_a_ms"] == 0 and prof["solve_ms"] == 0
+    assert a.L.rt_profile(a.h, 3) == rt.RT_ERR_INVALID     # unknown mode
     a.close()
     b.close()
 
