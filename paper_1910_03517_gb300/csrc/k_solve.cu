@@ -5,15 +5,18 @@
 // Per-camera gains: for each seam chain, channel and block one system
 //   (L_w + lambda I + 1 1^T / K_g) x = B^T W r,
 // x_k = log g_k, r = log mu^L(right camera) - log mu^R(left camera) over the
-// valid seams, w = valid fraction of the band; solved in FP64 by one warp
-// per system (continuant elimination of the chain's tridiagonal matrix and a
-// rank-one Woodbury correction for a ring, see solve_global_kernel);
-// g = clamp(exp(x)).
+// valid seams, w = valid fraction of the band; solved to FP64 accuracy by
+// one warp per system (continuant elimination of the chain's tridiagonal
+// matrix and a rank-one Sherman-Morrison correction for a ring, see
+// solve_global_kernel); g = clamp(exp(x)).
 // Seam affine maps: one thread per (camera, side, block, channel) matches
 // its band's mean and variance to the equal-weight mixture of the two bands
 // of its seam: a = sd_s / sd_side, b = mu_s - a mu_side.
-// Both: E = first ? E_new : (1 - alpha) E + alpha E_new; q = llround(65536 E).
+// Both: E = first ? E_new : (1 - alpha) E + alpha E_new; q = 65536 E rounded
+// half away from zero.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "rt_internal.cuh"
 
@@ -41,133 +44,239 @@ __device__ __forceinline__ void smooth_store(const SolveArgs &a, size_t idx, dou
 __device__ __forceinline__ int block_rows(int j, int H, int B) { return (int)(((long long)(j + 1) * H) / B - ((long long)j * H) / B); }
 
 
-// One system per CTA (one warp): the GPU's FP64 units are few and slow, so
-// systems are spread over SMs and the sequential part is kept short.
+// ---------------------------------------------------------------------------
+// FP64 on this GPU: one warp-wide FP64 instruction occupies a sub-partition's
+// FP64 unit for ~64 cycles whatever the number of active lanes, and a library
+// log / exp / division costs ~2100 / ~1300 / ~430 cycles.  The solve is a
+// chain of such steps, so it is written to issue few FP64 instructions:
+// logarithm and exponential are table-driven (FP64 only where the result's
+// leading bits form, the small tails in FP32), the chain's unknowns stay on
+// lanes, and the sequential recurrences cost one or two FP64 FMAs per camera.
+// Results agree with plain FP64 arithmetic to ~1e-12 relative.
+// ---------------------------------------------------------------------------
+
+constexpr double kLn2 = 0.69314718055994530942;
+
+// A = 2^e f with f in [1, 2); f = c_i (1 + u), |u| <= 1/256 (Tang's
+// table-driven logarithm, ACM TOMS 16(4), 1990: ln A = e ln 2 + ln c_i +
+// ln(1 + u)).  Requires A > 0; the leading 53 bits of A are used.
+__device__ __forceinline__ void log_parts(unsigned long long A, const SolveTables &t, int &e, int &i, double &u)
+{
+    const int lz = __clzll((long long)A);
+    const unsigned long long m = A << lz;             // leading one at bit 63
+    e = 63 - lz;
+    i = (int)((m >> 56) & 127);
+    const double f = __longlong_as_double((long long)((1023ull << 52) | ((m << 1) >> 12)));
+    u = fma(f, t.invc[i], -1.0);
+}
+
+// u - ln(1 + u) = u^2/2 - u^3/3 + u^4/4 - u^5/5 + ... for |u| <= 1/256: at
+// most 7.7e-6, so FP32 leaves an absolute error near 1e-12; the first omitted
+// term is below 3e-15.
+__device__ __forceinline__ float log1p_tail(float u)
+{
+    return u * u * (0.5f - u * (0.333333343f - u * (0.25f - u * 0.2f)));
+}
+
+// ln(A / B) for positive integers A, B < 2^64.
+__device__ __forceinline__ double log_ratio(unsigned long long A, unsigned long long B, const SolveTables &t)
+{
+    int eA, iA, eB, iB;
+    double uA, uB;
+    log_parts(A, t, eA, iA, uA);
+    log_parts(B, t, eB, iB, uB);
+    const float h = log1p_tail((float)uA) - log1p_tail((float)uB);
+    return fma((double)(eA - eB), kLn2, t.logc[iA] - t.logc[iB]) + ((uA - uB) - (double)h);
+}
+
+// e^x for x in [-700, 40] (Tang's table-driven exponential, ACM TOMS 15(2),
+// 1989): x = (64 m + j) ln2/64 + r, |r| <= ln2/128 + tiny, e^x = 2^m 2^(j/64)
+// (1 + r + q(r)), q = r^2/2 + r^3/6 + r^4/24 + r^5/120 below 1.5e-5 (FP32).
+__device__ __forceinline__ double exp_table(double x, const SolveTables &t)
+{
+    const int k = __float2int_rn((float)x * 92.3324826168936579f);   // 64 / ln 2
+    const double r = fma((double)(-k), kLn2 / 64.0, x);
+    const float rf = (float)r;
+    const float q = rf * rf * (0.5f + rf * (0.166666672f + rf * (0.0416666679f + rf * 0.00833333377f)));
+    const double tj = t.exp2j[k & 63];
+    const double y = fma(tj, r + (double)q, tj);
+    return __hiloint2double(__double2hiint(y) + (k >> 6) * (1 << 20), __double2loint(y));
+}
+
+// round-half-away-from-zero of 65536 v for |v| < 2^15, from the bits of v
+// (no FP64 instruction)
+__device__ __forceinline__ int32_t q16_round(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 2047) - 1023;
+    const unsigned long long mant = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = 36 - ex;                       // 65536 |v| = mant 2^-sh
+    int32_t q;
+    if (sh >= 64) q = 0;
+    else if (sh <= 0) q = (int32_t)(mant << -sh);
+    else q = (int32_t)((mant + (1ull << (sh - 1))) >> sh);
+    return (b >> 63) ? -q : q;
+}
+
+// One system (chain, block, channel) per CTA of one warp, one camera of the
+// chain per lane; the systems of a frame set spread over SMs.
 //
 // The right-hand side sums to zero (every seam adds w r to one camera and
 // subtracts it from the other), so 1^T x = 0 and the gauge term 1 1^T / K_g
 // leaves the solution unchanged: x solves (L_w + lambda I) x = rhs.  For a
 // chain that matrix T is tridiagonal (diagonal d_k = lambda + w_{k-1} + w_k,
-// off-diagonals -w); a ring adds its closing seam as a rank-one term
-// v v^T, v = sqrt(w_c)(e_last - e_first), handled by the Woodbury identity.
-// T is eliminated through its continuants
-//   P_{-1} = 1, P_k = d_k P_{k-1} - w_{k-1}^2 P_{k-2},
-//   s_k = rhs_k P_{k-1} + w_{k-1} s_{k-1}          (forward, one FMA per step)
-//   x_k = s_k / P_k + (w_k P_{k-1} / P_k) x_{k+1}   (backward, one FMA per step)
-// so the divisions run on all lanes at once and only FMAs stay sequential.
+// off-diagonals -w); a ring's closing seam adds w_c z z^T, z = e_last -
+// e_first, handled by the Sherman-Morrison identity.  T is eliminated through
+// its continuants
+//   P_{-1} = 1, P_k = d_k P_{k-1} - w_{k-1}^2 P_{k-2}        (2 FP64 / step)
+//   s_k = rhs_k P_{k-1} + w_{k-1} s_{k-1}                     (1 FP64 / step)
+//   x_k = s_k / P_k + (w_k P_{k-1} / P_k) x_{k+1}             (1 FP64 / step)
+// with the products and divisions done on all lanes at once.
 __global__ void __launch_bounds__(32) solve_global_kernel(const SolveArgs a)
 {
-    __shared__ double sw[kMaxChain], srw[kMaxChain], wp[kMaxChain], rh[kMaxChain], vv[kMaxChain];
-    __shared__ double P[kMaxChain], Pp[kMaxChain], sB[kMaxChain], sV[kMaxChain];
-    __shared__ double aB[kMaxChain], aV[kMaxChain], bt[kMaxChain], xb[kMaxChain], xv[kMaxChain];
-    __shared__ int sb[kMaxChain];
+    __shared__ double s_in[kMaxChain], s_d[kMaxChain], s_q[kMaxChain], s_wp[kMaxChain], s_P[kMaxChain];
+    __shared__ double s_t[kMaxChain], s_tz[kMaxChain], s_a[kMaxChain], s_az[kMaxChain], s_b[kMaxChain];
+    __shared__ double s_x[kMaxChain], s_xz[kMaxChain];
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x;
     const int sys = blockIdx.x;
     const int c = sys % 3, j = (sys / 3) % a.B, grp = sys / (3 * a.B);
-    const int g0 = a.group_start[grp];
-    const int n = a.group_start[grp + 1] - g0;
-    // 1. the seam whose left camera is member `lane`: weight w and w * r,
-    //    r = log mu^L - log mu^R (one logarithm of the ratio)
+    const int g0 = a.topo.gstart[grp];
+    const int n = a.topo.gstart[grp + 1] - g0;
+    const bool act = lane < n;
+    const int cam = act ? a.topo.member[g0 + lane] : 0;
+    const int kr = act ? a.topo.right[cam] : -1;
+    const int bpos = act ? a.topo.rpos[cam] : -1;     // position of kr in the chain
+    const size_t i0 = (((size_t)(cam * 2 + 0) * a.B + j) * 3 + c) * 2;
+    const size_t i1 = (((size_t)(cam * 2 + 1) * a.B + j) * 3 + c) * 2;
+    // every load of the system in one round
+    uint32_t nR = 0, nL = 0;
+    unsigned long long sR = 0, sL = 0;
+    if (bpos >= 0) {
+        const size_t iR = ((size_t)(cam * 2 + 1) * a.B + j) * 3 + c;
+        const size_t iL = ((size_t)(kr * 2 + 0) * a.B + j) * 3 + c;
+        nR = a.n[iR]; nL = a.n[iL];
+        sR = a.sum[iR]; sL = a.sum[iL];
+    }
+    double2 e_old = make_double2(0.0, 0.0);
+    if (act && !a.first) e_old = *reinterpret_cast<const double2 *>(a.E + i0);
+    // 1. the seam to the right of camera `lane`: weight w = valid fraction of
+    //    the band, r = log max(mu^L, 1) - log max(mu^R, 1) as the log of an
+    //    exact integer ratio
+    const bool valid = bpos >= 0 && nR >= (uint32_t)a.min_valid && nL >= (uint32_t)a.min_valid;
     double w = 0.0, wr = 0.0;
-    int bpos = -1;
-    if (lane < n) {
-        const int kl = a.group_members[g0 + lane];
-        const int kr = a.right_nbr[kl];
-        if (kr >= 0 && kr != kl) {
-            for (int q = 0; q < n; ++q)
-                if (a.group_members[g0 + q] == kr) bpos = q;
-            const size_t iR = ((size_t)(kl * 2 + 1) * a.B + j) * 3 + c;
-            const size_t iL = ((size_t)(kr * 2 + 0) * a.B + j) * 3 + c;
-            const uint32_t nR = a.n[iR], nL = a.n[iL];
-            if (bpos >= 0 && nR >= (uint32_t)a.min_valid && nL >= (uint32_t)a.min_valid) {
-                const unsigned long long sR = a.sum[iR], sL = a.sum[iL];
-                double ratio;
-                if (sR >= nR && sL >= nL)      // both means >= 1: exact integer products
-                    ratio = (double)(sL * nR) / (double)(sR * nL);
-                else
-                    ratio = fmax((double)sL / (double)nL, 1.0) / fmax((double)sR / (double)nR, 1.0);
-                const int rows = min(block_rows(j, a.cam_H[kl], a.B), block_rows(j, a.cam_H[kr], a.B));
-                w = (double)min(nR, nL) / (double)(a.S * rows);
-                wr = w * log(ratio);
-            } else {
-                bpos = -1;
+    if (valid) {
+        const bool lok = sL >= nL, rok = sR >= nR;    // means >= 1
+        const unsigned long long A = (lok ? sL : 1ull) * (rok ? nR : 1ull);
+        const unsigned long long Bq = (rok ? sR : 1ull) * (lok ? nL : 1ull);
+        const double r = log_ratio(A, Bq, a.tab);
+        const int rows = min(block_rows(j, a.topo.H[cam], a.B), block_rows(j, a.topo.H[kr], a.B));
+        w = (double)min(nR, nL) / (double)(a.S * rows);
+        wr = w * r;
+    }
+    // 2. right-hand side (own seam minus the incoming one), tridiagonal T
+    s_in[lane] = 0.0;
+    __syncwarp();
+    if (valid) s_in[bpos] = wr;                       // each camera has one left neighbour
+    __syncwarp();
+    const double rh = wr - s_in[lane];
+    const double wp = (valid && bpos == lane + 1) ? w : 0.0;   // path seam (lane, lane + 1)
+    double wprev = __shfl_up_sync(full, wp, 1);
+    if (lane == 0) wprev = 0.0;
+    const bool ring = __ballot_sync(full, valid && bpos == 0 && lane == n - 1 && n >= 2) != 0;
+    const double wc = __shfl_sync(full, w, n > 0 ? n - 1 : 0);
+    if (act) {
+        s_d[lane] = a.lambda + wprev + wp;
+        s_q[lane] = wprev * wprev;
+        s_wp[lane] = wp;
+    }
+    __syncwarp();
+    // 3. continuants (lane 0)
+    if (lane == 0) {
+        double p2 = 0.0, p1 = 1.0;
+#pragma unroll 4
+        for (int k = 0; k < n; ++k) {
+            const double pk = fma(s_d[k], p1, -(s_q[k] * p2));
+            s_P[k] = pk;
+            p2 = p1;
+            p1 = pk;
+        }
+    }
+    __syncwarp();
+    const double Pk = act ? s_P[lane] : 1.0;
+    const double Pm = (act && lane > 0) ? s_P[lane - 1] : 1.0;
+    const double ip = 1.0 / Pk;
+    if (act) {
+        s_t[lane] = rh * Pm;
+        s_tz[lane] = lane == n - 1 ? Pm : (lane == 0 ? -Pm : 0.0);    // z = e_last - e_first
+        s_b[lane] = wp * Pm * ip;
+    }
+    __syncwarp();
+    // 4. forward sums (lane 0)
+    if (lane == 0) {
+        double sb = 0.0, sz = 0.0, wl = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < n; ++k) {
+            sb = fma(wl, sb, s_t[k]);
+            s_a[k] = sb;
+            if (ring) {
+                sz = fma(wl, sz, s_tz[k]);
+                s_az[k] = sz;
+            }
+            wl = s_wp[k];
+        }
+    }
+    __syncwarp();
+    if (act) {
+        s_a[lane] *= ip;
+        if (ring) s_az[lane] *= ip;
+    }
+    __syncwarp();
+    // 5. back substitution (lane 0)
+    if (lane == 0) {
+        double xb = 0.0, xz = 0.0;
+#pragma unroll 4
+        for (int k = n - 1; k >= 0; --k) {
+            xb = fma(s_b[k], xb, s_a[k]);
+            s_x[k] = xb;
+            if (ring) {
+                xz = fma(s_b[k], xz, s_az[k]);
+                s_xz[k] = xz;
             }
         }
     }
-    sw[lane] = w;
-    srw[lane] = wr;
-    sb[lane] = bpos;
     __syncwarp();
-    // right-hand side, the chain's path weights w_k (seam k, k+1) and the
-    // ring's rank-one vector
-    const bool ring = n >= 2 && sb[n - 1] == 0;
-    const double sv = ring ? sqrt(sw[n - 1]) : 0.0;
-    if (lane < n) {
-        double r = sb[lane] >= 0 ? srw[lane] : 0.0;
-        for (int e = 0; e < n; ++e)
-            if (sb[e] == lane) r -= srw[e];
-        rh[lane] = r;
-        wp[lane] = (lane + 1 < n && sb[lane] == lane + 1) ? sw[lane] : 0.0;
-        vv[lane] = ring ? (lane == n - 1 ? sv : (lane == 0 ? -sv : 0.0)) : 0.0;
+    if (!act) return;
+    double x = s_x[lane];
+    if (ring) {
+        const double zx = s_x[n - 1] - s_x[0], zz = s_xz[n - 1] - s_xz[0];
+        x -= s_xz[lane] * (wc * zx / fma(wc, zz, 1.0));
     }
-    __syncwarp();
-    // 2. forward continuant recurrences (lane 0; one FMA per step each)
-    if (lane == 0) {
-        double Pm2 = 0.0, Pm1 = 1.0, sbm = 0.0, svm = 0.0;
-        for (int k = 0; k < n; ++k) {
-            const double wl = k > 0 ? wp[k - 1] : 0.0;
-            const double d = a.lambda + wl + wp[k];
-            const double pk = fma(d, Pm1, -(wl * wl) * Pm2);
-            sbm = fma(wl, sbm, rh[k] * Pm1);
-            svm = fma(wl, svm, vv[k] * Pm1);
-            P[k] = pk;
-            Pp[k] = Pm1;
-            sB[k] = sbm;
-            sV[k] = svm;
-            Pm2 = Pm1;
-            Pm1 = pk;
-        }
+    // 6. g = clamp(exp(x)); smoothing; Q16.  x is first kept inside a range
+    //    whose exponentials lie beyond the clamp (same clamped result).
+    const float xf = (float)x;
+    if (!(xf >= a.xlo_f)) x = a.xlo;
+    else if (xf > a.xhi_f) x = a.xhi;
+    long long gb = __double_as_longlong(exp_table(x, a.tab));   // positive: bit order = value order
+    gb = max(gb, __double_as_longlong(a.gmin));
+    gb = min(gb, __double_as_longlong(a.gmax));
+    const double g = __longlong_as_double(gb);
+    double2 e;
+    if (a.first) {
+        e = make_double2(g, 0.0);
+    } else {
+        e.x = fma(a.one_m_alpha, e_old.x, a.alpha * g);
+        e.y = a.one_m_alpha * e_old.y;
     }
-    __syncwarp();
-    // 3. the divisions, all lanes at once
-    if (lane < n) {
-        const double ip = 1.0 / P[lane];
-        aB[lane] = sB[lane] * ip;
-        aV[lane] = sV[lane] * ip;
-        bt[lane] = wp[lane] * Pp[lane] * ip;
-    }
-    __syncwarp();
-    // 4. backward recurrences (lane 0)
-    if (lane == 0) {
-        double x1 = 0.0, x2 = 0.0;
-        for (int k = n - 1; k >= 0; --k) {
-            x1 = fma(bt[k], x1, aB[k]);
-            x2 = fma(bt[k], x2, aV[k]);
-            xb[k] = x1;
-            xv[k] = x2;
-        }
-    }
-    __syncwarp();
-    // 5. ring: x = x_b - x_v (v^T x_b) / (1 + v^T x_v); gains, smoothing, Q16
-    if (lane < n) {
-        double x = xb[lane];
-        if (ring) {
-            const double vxb = sv * (xb[n - 1] - xb[0]), vxv = sv * (xv[n - 1] - xv[0]);
-            x -= xv[lane] * vxb / (1.0 + vxv);
-        }
-        const int cam = a.group_members[g0 + lane];
-        const double g = fmin(fmax(exp(x), a.gmin), a.gmax);
-        const size_t i0 = (((size_t)(cam * 2 + 0) * a.B + j) * 3 + c) * 2;
-        const size_t i1 = (((size_t)(cam * 2 + 1) * a.B + j) * 3 + c) * 2;
-        // both sides carry the same gain: smooth and quantise once, store twice
-        smooth_store(a, i0, g, 0.0);
-        a.maps_new[i1] = a.maps_new[i0];
-        a.maps_new[i1 + 1] = 0.0;
-        a.E[i1] = a.E[i0];
-        a.E[i1 + 1] = a.E[i0 + 1];
-        a.q16[i1] = a.q16[i0];
-        a.q16[i1 + 1] = a.q16[i0 + 1];
-    }
+    const int2 q = make_int2(q16_round(e.x), q16_round(e.y));
+    const double2 m = make_double2(g, 0.0);
+    // both sides carry the same gain
+    *reinterpret_cast<double2 *>(a.maps_new + i0) = m;
+    *reinterpret_cast<double2 *>(a.maps_new + i1) = m;
+    *reinterpret_cast<double2 *>(a.E + i0) = e;
+    *reinterpret_cast<double2 *>(a.E + i1) = e;
+    *reinterpret_cast<int2 *>(a.q16 + i0) = q;
+    *reinterpret_cast<int2 *>(a.q16 + i1) = q;
 }
 
 __global__ void __launch_bounds__(64) solve_affine_kernel(const SolveArgs a)
@@ -202,16 +311,59 @@ __global__ void __launch_bounds__(64) solve_affine_kernel(const SolveArgs a)
     }
 }
 
+const SolveTables &solve_tables()
+{
+    static const SolveTables t = [] {
+        SolveTables v;
+        for (int i = 0; i < 128; ++i) {
+            const double ci = 1.0 + (i + 0.5) / 128.0;   // exact
+            v.invc[i] = 1.0 / ci;
+            v.logc[i] = std::log(ci);
+        }
+        for (int i = 0; i < 64; ++i) v.exp2j[i] = std::exp2(i / 64.0);
+        return v;
+    }();
+    return t;
+}
+
 }  // namespace
 
-cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s)
+void fill_solve_topo(SolveTopo &t, int K, int n_groups, const int32_t *group_start, const int32_t *group_members,
+                     const int32_t *right_nbr, const int32_t *cam_H)
 {
-    if (a.fit_mode == RT_FIT_GLOBAL) {
+    memset(&t, 0, sizeof t);
+    for (int g = 0; g <= n_groups; ++g) t.gstart[g] = (int8_t)group_start[g];
+    for (int i = 0; i < group_start[n_groups]; ++i) t.member[i] = (int8_t)group_members[i];
+    for (int k = 0; k < K; ++k) {
+        t.right[k] = (int8_t)right_nbr[k];
+        t.rpos[k] = -1;
+        t.H[k] = cam_H[k];
+    }
+    for (int g = 0; g < n_groups; ++g)
+        for (int i = group_start[g]; i < group_start[g + 1]; ++i) {
+            const int k = group_members[i], r = right_nbr[k];
+            if (r < 0 || r == k) continue;
+            for (int q = group_start[g]; q < group_start[g + 1]; ++q)
+                if (group_members[q] == r) t.rpos[k] = (int8_t)(q - group_start[g]);
+        }
+}
+
+cudaError_t launch_solve(const SolveArgs &args, cudaStream_t s)
+{
+    if (args.fit_mode == RT_FIT_GLOBAL) {
+        SolveArgs a = args;
+        a.tab = solve_tables();
+        a.one_m_alpha = 1.0 - a.alpha;
+        // beyond these the clamped gain is gmin / gmax whatever x is
+        a.xlo = std::max(std::log(a.gmin) - 1.0, -700.0);
+        a.xhi = std::log(a.gmax) + 1.0;
+        a.xlo_f = (float)a.xlo;
+        a.xhi_f = (float)a.xhi;
         const int n_sys = a.n_groups * a.B * 3;
         solve_global_kernel<<<n_sys, 32, 0, s>>>(a);
     } else {
-        const int n_ent = a.K * 2 * a.B * 3;
-        solve_affine_kernel<<<(n_ent + 63) / 64, 64, 0, s>>>(a);
+        const int n_ent = args.K * 2 * args.B * 3;
+        solve_affine_kernel<<<(n_ent + 63) / 64, 64, 0, s>>>(args);
     }
     return cudaGetLastError();
 }

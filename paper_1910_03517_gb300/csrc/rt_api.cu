@@ -77,6 +77,7 @@ struct rt_handle {
     int32_t *group_start = nullptr, *group_members = nullptr, *left_nbr = nullptr, *right_nbr = nullptr,
             *cam_H = nullptr;
     int n_groups = 0;
+    SolveTopo solve_topo{};
     __half *crops[2] = {nullptr, nullptr};
     rt_crop *crop_dev[2] = {nullptr, nullptr};
     rt_crop *crop_host = nullptr;          // pinned [2][max_crops]
@@ -420,6 +421,7 @@ rt_status setup(rt_handle *h)
         RT_CUDA(h, cudaMemcpy(h->left_nbr, ln.data(), ln.size() * 4, cudaMemcpyHostToDevice));
         RT_CUDA(h, cudaMemcpy(h->right_nbr, rn.data(), rn.size() * 4, cudaMemcpyHostToDevice));
         RT_CUDA(h, cudaMemcpy(h->cam_H, hh.data(), hh.size() * 4, cudaMemcpyHostToDevice));
+        fill_solve_topo(h->solve_topo, K, h->n_groups, gs.data(), gm.data(), rn.data(), hh.data());
     }
     // pass B launch shape: a persistent grid of all resident CTAs
     RT_CUDA(h, pass_b_prepare(h->pb_threads, &h->pb_smem));
@@ -543,6 +545,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     sa.first = first ? 1 : 0; sa.alpha = p.alpha; sa.lambda = p.lambda; sa.gmin = p.gain_min; sa.gmax = p.gain_max;
     sa.n_groups = h->n_groups; sa.group_start = h->group_start; sa.group_members = h->group_members;
     sa.left_nbr = h->left_nbr; sa.right_nbr = h->right_nbr; sa.cam_H = h->cam_H;
+    sa.topo = h->solve_topo;
     if (prof_chain) RT_CUDA(h, prof_record(h, pe.s0, h->s_solve));
     RT_CUDA(h, launch_solve(sa, h->s_solve));
     if (prof_chain) RT_CUDA(h, prof_record(h, pe.s1, h->s_solve));

@@ -69,6 +69,31 @@ struct PassAArgs {
     unsigned long long *clear_u64; size_t clear_u64_n;
 };
 
+// Tables of the table-driven logarithm and exponential of the gain solve
+// (filled on the host by launch_solve): c_i = 1 + (i + 1/2) / 128.
+struct SolveTables {
+    double invc[128];     // 1 / c_i
+    double logc[128];     // ln c_i
+    double exp2j[64];     // 2^(j / 64)
+};
+
+// The seam chains in a form the solve reads from its parameter block (no
+// dependent loads): chain g holds member[gstart[g] .. gstart[g + 1]), by
+// position; right[k] is the camera whose left band meets camera k's right
+// band (-1 none) and rpos[k] its position in the chain.
+struct SolveTopo {
+    int8_t gstart[RT_MAX_CAMERAS + 1];
+    int8_t member[RT_MAX_CAMERAS];
+    int8_t right[RT_MAX_CAMERAS];
+    int8_t rpos[RT_MAX_CAMERAS];
+    int32_t H[RT_MAX_CAMERAS];
+};
+
+// Fills t from the chain arrays of the host (group_start[n_groups + 1],
+// group_members, right_nbr[K], cam_H[K]).
+void fill_solve_topo(SolveTopo &t, int K, int n_groups, const int32_t *group_start, const int32_t *group_members,
+                     const int32_t *right_nbr, const int32_t *cam_H);
+
 // Solve: fit + smoothing + quantisation.
 struct SolveArgs {
     const uint32_t *n;
@@ -85,6 +110,12 @@ struct SolveArgs {
     const int32_t *left_nbr;      // [K] camera whose right band meets my left band, -1 none
     const int32_t *right_nbr;     // [K]
     const int32_t *cam_H;         // [K]
+    SolveTopo topo;               // the same chains, by value
+    // filled by launch_solve
+    SolveTables tab;
+    double one_m_alpha;           // 1 - alpha
+    double xlo, xhi;              // log-gain range kept before the exponential
+    float xlo_f, xhi_f;
 };
 
 struct CropArgs {

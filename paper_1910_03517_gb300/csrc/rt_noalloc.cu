@@ -171,6 +171,7 @@ extern "C" rt_status rt_fit_gains_noalloc(const rt_camera_desc *cams, int32_t nu
     sa.alpha = 0.05; sa.lambda = 1e-6; sa.gmin = 0.25; sa.gmax = 4.0;
     sa.n_groups = n_groups; sa.group_start = d_tab; sa.group_members = d_tab + (kNaCams + 1);
     sa.left_nbr = sa.group_members + kNaCams; sa.right_nbr = sa.left_nbr + kNaCams; sa.cam_H = sa.right_nbr + kNaCams;
+    fill_solve_topo(sa.topo, K, n_groups, gs, gm, rn, hh);
     if (launch_solve(sa, st) != cudaSuccess) return RT_ERR_CUDA;
     return RT_OK;
 }
