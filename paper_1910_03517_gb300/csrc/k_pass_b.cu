@@ -290,7 +290,7 @@ constexpr int kHistWords = 3 * 256 * kHistLanes;
 constexpr int kThumbWords = RT_THUMB_H * RT_THUMB_W * 3;
 
 template <int FIT, bool STATS, bool THUMBS>
-__global__ void __launch_bounds__(THUMBS ? 512 : 1024, 1) pass_b_kernel(const ArrayGeom g, const PassBArgs a)
+__global__ void __launch_bounds__(THUMBS ? 512 : RT_PASS_B_THREADS, 1) pass_b_kernel(const ArrayGeom g, const PassBArgs a)
 {
     extern __shared__ uint32_t sh[];
     uint32_t *th = sh + (STATS ? kHistWords : 0);   // [36][64][3] cell sums (THUMBS)

@@ -11,6 +11,12 @@
 
 namespace rt {
 
+// Threads of a pass B CTA (one persistent CTA per SM); the register budget
+// per thread follows from it (65536 / threads).
+#ifndef RT_PASS_B_THREADS
+#define RT_PASS_B_THREADS 1024
+#endif
+
 constexpr int kUnitCols = 16;          // columns a thread converts per row
 constexpr int kHistLanes = 32;         // lane-private copies of each histogram bin
 
