@@ -33,6 +33,12 @@ __device__ __forceinline__ uint4 ld_stream(const uint8_t *p)
     return v;
 }
 
+// Programmatic dependent launch: the next pass B may be scheduled while this
+// one runs (its CTAs take SMs as this grid's CTAs exit); it waits for this
+// grid's completion, memory included, before touching the accumulators.
+__device__ __forceinline__ void allow_next_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void wait_prev_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void red_shared_inc(uint32_t addr)
 {
     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
@@ -296,9 +302,7 @@ __global__ void __launch_bounds__(THUMBS ? 512 : RT_PASS_B_THREADS, 1) pass_b_ke
     uint32_t *th = sh + (STATS ? kHistWords : 0);   // [36][64][3] cell sums (THUMBS)
     const int tid = threadIdx.x;
     const ConvConsts &k = g.conv;
-    // clear the accumulators the next frame set will use (other parity)
-    for (uint32_t i = blockIdx.x * blockDim.x + tid; i < a.clear_a_n; i += gridDim.x * blockDim.x) a.clear_a[i] = 0u;
-    for (uint32_t i = blockIdx.x * blockDim.x + tid; i < a.clear_b_n; i += gridDim.x * blockDim.x) a.clear_b[i] = 0u;
+    allow_next_launch();
     // balanced contiguous slices: q units each, the first r slices one more
     const uint32_t q = g.units_total / gridDim.x, r = g.units_total - q * gridDim.x;
     uint32_t ub = blockIdx.x * q + min(blockIdx.x, r);
@@ -363,6 +367,7 @@ __global__ void __launch_bounds__(THUMBS ? 512 : RT_PASS_B_THREADS, 1) pass_b_ke
                 }
             }
         }
+        if (STATS || THUMBS) wait_prev_grid();   // the previous pass B cleared these accumulators
         if (THUMBS) {
             __syncthreads();
             // [36][64][3] shared -> [3][36][64] global
@@ -390,6 +395,11 @@ __global__ void __launch_bounds__(THUMBS ? 512 : RT_PASS_B_THREADS, 1) pass_b_ke
         ub = se;
         ++cam;
     }
+    // clear the accumulators the next frame set will use (other parity);
+    // the previous pass B flushed its sums into them
+    wait_prev_grid();
+    for (uint32_t i = blockIdx.x * blockDim.x + tid; i < a.clear_a_n; i += gridDim.x * blockDim.x) a.clear_a[i] = 0u;
+    for (uint32_t i = blockIdx.x * blockDim.x + tid; i < a.clear_b_n; i += gridDim.x * blockDim.x) a.clear_b[i] = 0u;
 }
 
 template <int FIT, bool STATS, bool THUMBS>
@@ -398,8 +408,17 @@ cudaError_t launch_one(const ArrayGeom &g, const PassBArgs &a, int grid, int thr
     const size_t smem = (size_t)((STATS ? kHistWords : 0) + (THUMBS ? kThumbWords : 0)) * 4;
     // the thumbnail variant is compiled for at most 512 threads per CTA
     if (THUMBS && threads > 512) threads = 512;
-    pass_b_kernel<FIT, STATS, THUMBS><<<grid, threads, smem, s>>>(g, a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pass_b_kernel<FIT, STATS, THUMBS>, g, a);
 }
 
 template <int FIT>

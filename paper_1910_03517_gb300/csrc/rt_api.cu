@@ -568,7 +568,8 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
         }
     }
     // accumulators of this parity were cleared by pass B of the previous
-    // frame set (or at allocation); this pass B clears the other parity
+    // frame set (or at allocation); this pass B clears the other parity at
+    // its end (it may start before the previous one ends, see k_pass_b.cu)
     uint32_t *fh = (p.flags & RT_FLAG_FRAME_STATS) ? h->frame_hist[par] : nullptr;
     uint32_t *th = (p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[par] : nullptr;
     PassBArgs pb{};
