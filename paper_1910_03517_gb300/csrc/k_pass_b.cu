@@ -296,7 +296,7 @@ constexpr int kHistWords = 3 * 256 * kHistLanes;
 constexpr int kThumbWords = RT_THUMB_H * RT_THUMB_W * 3;
 
 template <int FIT, bool STATS, bool THUMBS>
-__global__ void __launch_bounds__(THUMBS ? 512 : RT_PASS_B_THREADS, 1) pass_b_kernel(const ArrayGeom g, const PassBArgs a)
+__global__ void __launch_bounds__(THUMBS ? 512 : RT_PASS_B_THREADS, THUMBS ? 1 : RT_PASS_B_CTAS_PER_SM) pass_b_kernel(const ArrayGeom g, const PassBArgs a)
 {
     extern __shared__ uint32_t sh[];
     uint32_t *th = sh + (STATS ? kHistWords : 0);   // [36][64][3] cell sums (THUMBS)
@@ -406,8 +406,10 @@ template <int FIT, bool STATS, bool THUMBS>
 cudaError_t launch_one(const ArrayGeom &g, const PassBArgs &a, int grid, int threads, cudaStream_t s)
 {
     const size_t smem = (size_t)((STATS ? kHistWords : 0) + (THUMBS ? kThumbWords : 0)) * 4;
-    // the thumbnail variant is compiled for at most 512 threads per CTA
+    // the thumbnail variant is compiled for at most 512 threads per CTA and
+    // its shared memory leaves room for one CTA per SM
     if (THUMBS && threads > 512) threads = 512;
+    if (THUMBS && STATS && grid >= RT_PASS_B_CTAS_PER_SM) grid /= RT_PASS_B_CTAS_PER_SM;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(threads);
@@ -428,6 +430,8 @@ cudaError_t prepare_fit()
     const int full = (kHistWords + kThumbWords) * 4;
     if ((e = cudaFuncSetAttribute(pass_b_kernel<FIT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kHistWords * 4)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(pass_b_kernel<FIT, true, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  100)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(pass_b_kernel<FIT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   full)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(pass_b_kernel<FIT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -425,7 +425,7 @@ rt_status setup(rt_handle *h)
     }
     // pass B launch shape: a persistent grid of all resident CTAs
     RT_CUDA(h, pass_b_prepare(h->pb_threads, &h->pb_smem));
-    h->pb_grid = h->sm_count;
+    h->pb_grid = h->sm_count * RT_PASS_B_CTAS_PER_SM;
     RT_CUDA(h, cudaDeviceSynchronize());
     return RT_OK;
 }
@@ -508,8 +508,15 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     const bool dep2 = h->capturing ? (t - 2 >= h->cap_t0) : (t >= 2 && h->launched[ev2]);
     // pass A(t) clears the slot the solve of frame set t-2 read
     if (dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_stats, h->ev_solved[ev2], 0));
-    // solve(t) overwrites the Q16 slot pass B(t-3) / B(t-2) (lagged) read
-    if (dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_solve, h->ev_done[ev2], 0));
+    // solve(t) overwrites the Q16 slot pass B(t-3) read (current schedule)
+    // or pass B(t-2) read (lagged: pass B(t-2) applies solve(t-3)'s slot)
+    if (p.schedule == RT_SCHED_LAGGED) {
+        if (dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_solve, h->ev_done[ev2], 0));
+    } else {
+        const int ev3 = (int)((t + kEvRing - 3) % kEvRing);
+        const bool dep3 = h->capturing ? (t - 3 >= h->cap_t0) : (t >= 3 && h->launched[ev3]);
+        if (dep3) RT_CUDA(h, cudaStreamWaitEvent(h->s_solve, h->ev_done[ev3], 0));
+    }
     if (!h->capturing && t >= 2 && h->out_launched[ev2])
         RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_out[ev2], 0));
     ProfEv pe{};

@@ -11,10 +11,16 @@
 
 namespace rt {
 
-// Threads of a pass B CTA (one persistent CTA per SM); the register budget
-// per thread follows from it (65536 / threads).
+// Pass B runs as a persistent grid of RT_PASS_B_CTAS_PER_SM CTAs per SM of
+// RT_PASS_B_THREADS threads each (each CTA holds its own 96 KB of
+// histograms; 64 registers a thread).  Two CTAs of 512 beat one of 1024:
+// their barriers and tails do not stall each other, and the next pass B
+// takes over an SM half at a time.
 #ifndef RT_PASS_B_THREADS
-#define RT_PASS_B_THREADS 1024
+#define RT_PASS_B_THREADS 512
+#endif
+#ifndef RT_PASS_B_CTAS_PER_SM
+#define RT_PASS_B_CTAS_PER_SM 2
 #endif
 
 constexpr int kUnitCols = 16;          // columns a thread converts per row
