@@ -19,6 +19,7 @@
 #include <cstring>
 
 #include "rt_internal.cuh"
+#include "../../include/rt_check.h"
 
 namespace rt {
 
@@ -45,7 +46,7 @@ __device__ __forceinline__ int block_rows(int j, int H, int B) { return (int)(((
 
 
 // ---------------------------------------------------------------------------
-// FP64 on this GPU: one warp-wide FP64 instruction occupies a sub-partition's
+// FP64 on GB300: one warp-wide FP64 instruction occupies a sub-partition's
 // FP64 unit for ~64 cycles whatever the number of active lanes, and a library
 // log / exp / division costs ~2100 / ~1300 / ~430 cycles.  The solve is a
 // chain of such steps, so it is written to issue few FP64 instructions:
@@ -85,7 +86,8 @@ __device__ __forceinline__ double log_ratio(unsigned long long A, unsigned long 
     double uA, uB;
     log_parts(A, t, eA, iA, uA);
     log_parts(B, t, eB, iB, uB);
-    const float h = log1p_tail((float)uA) - log1p_tail((float)uB);
+    // no contraction into an FMA: equal arguments give exactly 0
+    const float h = __fsub_rn(log1p_tail((float)uA), log1p_tail((float)uB));
     return fma((double)(eA - eB), kLn2, t.logc[iA] - t.logc[iB]) + ((uA - uB) - (double)h);
 }
 
@@ -369,3 +371,48 @@ cudaError_t launch_solve(const SolveArgs &args, cudaStream_t s)
 }
 
 }  // namespace rt
+
+namespace {
+
+__global__ void check_math_kernel(int n, const unsigned long long *a, const unsigned long long *b, double *lr,
+                                  const double *x, double *ex, const rt::SolveTables tab)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (lr) lr[i] = rt::log_ratio(a[i], b[i], tab);
+        if (ex) ex[i] = rt::exp_table(x[i], tab);
+    }
+}
+
+}  // namespace
+
+extern "C" rt_status rt_check_solve_math(int32_t n, const uint64_t *a, const uint64_t *b, double *log_ratio,
+                                         const double *x, double *exp_x)
+{
+    if (n < 0) return RT_ERR_INVALID;
+    if (n == 0) return RT_OK;
+    const bool do_log = a && b && log_ratio, do_exp = x && exp_x;
+    for (int i = 0; i < n; ++i) {
+        if (do_log && (a[i] == 0 || b[i] == 0)) return RT_ERR_INVALID;
+        if (do_exp && !(x[i] >= -700.0 && x[i] <= 700.0)) return RT_ERR_INVALID;
+    }
+    const size_t bytes = (size_t)n * 8;
+    unsigned char *d = nullptr;
+    if (cudaMalloc(&d, 5 * bytes) != cudaSuccess) return RT_ERR_CUDA;
+    unsigned long long *da = reinterpret_cast<unsigned long long *>(d), *db = da + n;
+    double *dl = reinterpret_cast<double *>(db + n), *dx = dl + n, *de = dx + n;
+    cudaError_t e = cudaSuccess;
+    if (do_log) {
+        e = cudaMemcpy(da, a, bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(db, b, bytes, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && do_exp) e = cudaMemcpy(dx, x, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        check_math_kernel<<<(n + 255) / 256, 256>>>(n, da, db, do_log ? dl : nullptr, dx, do_exp ? de : nullptr,
+                                                    rt::solve_tables());
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && do_log) e = cudaMemcpy(log_ratio, dl, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && do_exp) e = cudaMemcpy(exp_x, de, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? RT_OK : RT_ERR_CUDA;
+}

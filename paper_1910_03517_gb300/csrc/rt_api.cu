@@ -335,7 +335,9 @@ rt_status setup(rt_handle *h)
     }
     for (int i = 0; i < 2; ++i) {
         rt_status s;
-        if ((s = dalloc(h, &h->rgb[i], off)) != RT_OK) return s;
+        // 64 bytes of tail padding: the crop kernel reads aligned 16-byte
+        // groups around a window's last pixel
+        if ((s = dalloc(h, &h->rgb[i], off + 64)) != RT_OK) return s;
         if ((s = dalloc(h, &h->frame_hist[i], (size_t)K * 768)) != RT_OK) return s;
         if ((p.flags & RT_FLAG_THUMBNAILS) &&
             (s = dalloc(h, &h->thumbs[i], (size_t)K * 3 * RT_THUMB_H * RT_THUMB_W)) != RT_OK) return s;

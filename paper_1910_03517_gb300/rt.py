@@ -101,12 +101,30 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rt_get_thumb_features.argtypes = [c_vp, c_vp, c_i32]
     L.rt_destroy.argtypes = [c_vp]
     L.rt_destroy.restype = None
+    L.rt_check_solve_math.argtypes = [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]
+    L.rt_check_solve_math.restype = c_i32
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is ctypes.c_int:   # default restype: rt_status
             fn.restype = c_i32
     _lib = L
     return L
+
+
+def check_solve_math(a: np.ndarray, b: np.ndarray, x: np.ndarray):
+    """(ln(a/b), e^x) from the gain solve's device routines (include/rt_check.h)."""
+    L = load()
+    a = np.ascontiguousarray(a, np.uint64)
+    b = np.ascontiguousarray(b, np.uint64)
+    x = np.ascontiguousarray(x, np.float64)
+    n = len(a)
+    assert len(b) == n and len(x) == n
+    lr = np.zeros(n, np.float64)
+    ex = np.zeros(n, np.float64)
+    st = L.rt_check_solve_math(n, a.ctypes.data, b.ctypes.data, lr.ctypes.data, x.ctypes.data, ex.ctypes.data)
+    if st != RT_OK:
+        raise RtError(st, "rt_check_solve_math")
+    return lr, ex
 
 
 class RtError(RuntimeError):
