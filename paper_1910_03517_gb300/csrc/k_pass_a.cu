@@ -32,13 +32,35 @@ __device__ __forceinline__ uint4 ld16_any(const uint8_t *p)
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// Two conversions' rounding step in one packed FP32x2 FMA: bits of
+// (2^23 + 255 z) for z = z0, z1 (each already saturated to [0, 1]).
+__device__ __forceinline__ void magic2(float z0, float z1, uint32_t &b0, uint32_t &b1)
+{
+    asm("{\n .reg .b64 a, k, m, r;\n"
+        " mov.b64 a, {%2, %3};\n"
+        " mov.b64 k, {%4, %4};\n"
+        " mov.b64 m, {%5, %5};\n"
+        " fma.rn.f32x2 r, a, k, m;\n"
+        " mov.b64 {%0, %1}, r;\n}\n"
+        : "=r"(b0), "=r"(b1) : "f"(z0), "f"(z1), "f"(255.0f), "f"(kMagic));
+}
+
+// Histogram slot of value bits vb (channel c) for a pixel that passed the
+// motion test (ok): the bin, or the spare slot 768 for a moving pixel or a
+// saturated value (0 or 255) -- no branch per pixel.
+__device__ __forceinline__ uint32_t slot_of(uint32_t vb, int c, bool ok)
+{
+    const uint32_t v = vb - kMagicBits;
+    return (ok && v - 1u < 254u) ? (uint32_t)c * 256u + v : 768u;
+}
+
 __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const PassAArgs a, int Hmax)
 {
-    __shared__ uint32_t sh[3 * 256];
+    __shared__ uint32_t sh[3 * 256 + 1];   // + the spare slot
     const StripItem it = a.items[blockIdx.x];
     const CamGeom &cg = g.cam[it.cam];
     const ConvConsts &k = g.conv;
-    for (int i = threadIdx.x; i < 768; i += blockDim.x) sh[i] = 0;
+    for (int i = threadIdx.x; i < 769; i += blockDim.x) sh[i] = 0;
     {
         const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
         for (size_t i = tid; i < a.clear_u32_n; i += nt) a.clear_u32[i] = 0u;
@@ -66,13 +88,16 @@ __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const Pa
                 const float Vf = byte_f(uvw[p >> 1], (p & 1) * 2 + 1);
                 const float cz[3] = {fmaf(Vf, k.krv, k.c_r0), fmaf(Uf, k.kgu, fmaf(Vf, k.kgv, k.c_g0)),
                                      fmaf(Uf, k.kbu, k.c_b0)};
+                const float Y0f = byte_f(luma[p >> 1], 2 * (p & 1)), Y1f = byte_f(luma[p >> 1], 2 * (p & 1) + 1);
+                float z0[3], z1[3];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int i = 2 * p + q;
-                    const float Yf = byte_f(luma[i >> 2], i & 3);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) vb[i][c] = zbits(Yf, k.ky, cz[c]);
+                for (int c = 0; c < 3; ++c) {
+                    z0[c] = __saturatef(fmaf(Y0f, k.ky, cz[c]));
+                    z1[c] = __saturatef(fmaf(Y1f, k.ky, cz[c]));
                 }
+                magic2(z0[0], z0[1], vb[2 * p][0], vb[2 * p][1]);
+                magic2(z1[0], z1[1], vb[2 * p + 1][0], vb[2 * p + 1][1]);
+                magic2(z0[2], z1[2], vb[2 * p][2], vb[2 * p + 1][2]);
             }
         } else {
             const uint8_t *p = cg.y + (size_t)y * cg.y_pitch + 2 * x0;
@@ -94,16 +119,13 @@ __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const Pa
             const uint4 P = ld16(a.prev_luma + lo);
             prev[0] = P.x; prev[1] = P.y; prev[2] = P.z; prev[3] = P.w;
         }
+        const float T = (float)a.T;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            const int d = (int)((luma[i >> 2] >> (8 * (i & 3))) & 255u) - (int)((prev[i >> 2] >> (8 * (i & 3))) & 255u);
-            if (d > a.T || d < -a.T) continue;
+            const float d = byte_f(luma[i >> 2], i & 3) - byte_f(prev[i >> 2], i & 3);   // exact
+            const bool ok = fabsf(d) <= T;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const uint32_t v = vb[i][c] - kMagicBits;
-                if (v == 0u || v == 255u) continue;
-                atomicAdd(&sh[c * 256 + v], 1u);
-            }
+            for (int c = 0; c < 3; ++c) atomicAdd(&sh[slot_of(vb[i][c], c, ok)], 1u);
         }
     }
     __syncthreads();

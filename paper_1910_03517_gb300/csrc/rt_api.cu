@@ -32,7 +32,10 @@ namespace {
 
 constexpr int kEvRing = 4;
 constexpr int kQRing = 3;
-constexpr int kStripRows = 64;      // rows of one pass-A work item
+#ifndef RT_STRIP_ROWS
+#define RT_STRIP_ROWS 32
+#endif
+constexpr int kStripRows = RT_STRIP_ROWS;   // rows of one pass-A work item
 constexpr uint32_t kStateMagic = 0x52545331u;
 constexpr int kMaxProfiled = 4096;  // frame sets whose pass times one collection keeps
 
