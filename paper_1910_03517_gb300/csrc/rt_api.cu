@@ -116,7 +116,7 @@ struct rt_handle {
     // pass B launch shape
     // one pass-B CTA per SM: 896 x 64 registers leave room for pass A and the
     // solve of the next frame set to run beside it
-    int pb_grid = 0, pb_threads = RT_PASS_B_THREADS;
+    int pb_grid = 0, pb_threads = RT_PASS_B_RUN_THREADS;
     size_t pb_smem = 0;
     std::string err;
     size_t n_maps = 0;             // K*2*B*3*2

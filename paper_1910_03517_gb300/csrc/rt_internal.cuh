@@ -11,16 +11,25 @@
 
 namespace rt {
 
-// Pass B runs as a persistent grid of RT_PASS_B_CTAS_PER_SM CTAs per SM of
-// RT_PASS_B_THREADS threads each (each CTA holds its own 96 KB of
-// histograms; 64 registers a thread).  Two CTAs of 512 beat one of 1024:
-// their barriers and tails do not stall each other, and the next pass B
-// takes over an SM half at a time.
+// Pass B runs as a persistent grid of RT_PASS_B_CTAS_PER_SM CTAs per SM,
+// compiled for RT_PASS_B_THREADS threads (64 registers a thread) and
+// launched with RT_PASS_B_RUN_THREADS; each CTA holds its own 96 KB of
+// histograms.  Two CTAs per SM beat one: their barriers and tails do not
+// stall each other, and the next pass B takes over an SM half at a time.
+// Launching 384 of the 512 threads leaves 16K registers per SM to the band
+// statistics and the solve of the next frame set, which then run beside
+// pass B instead of waiting for its CTAs to exit.
 #ifndef RT_PASS_B_THREADS
 #define RT_PASS_B_THREADS 512
 #endif
 #ifndef RT_PASS_B_CTAS_PER_SM
 #define RT_PASS_B_CTAS_PER_SM 2
+#endif
+// Threads a pass B CTA is launched with (at most RT_PASS_B_THREADS, which
+// sets the register budget): fewer leave registers on each SM for the
+// statistics chain of the next frame set to run beside pass B.
+#ifndef RT_PASS_B_RUN_THREADS
+#define RT_PASS_B_RUN_THREADS 384
 #endif
 
 constexpr int kUnitCols = 16;          // columns a thread converts per row
