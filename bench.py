@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--timing-events", default="pass_b", choices=["pass_b", "all", "none"],
                     help="CUDA events inside the timed graph: around pass B only (the roofline's "
                          "timing), around every pass, or none (no roofline timing)")
@@ -388,6 +389,18 @@ def run_ours(args):
     for _ in range(1 + max(0, singles)):
         submit_one()
     arr.sync()
+    # launch shapes: timed on this ring (untimed here), cached per device and array
+    tuning = None
+    if not args.no_autotune:
+        order = [(t_sub[0] + j) % ring for j in range(ring)]
+        cache = os.path.join(tempfile.gettempdir(), "rt_tuning_%d.json" % os.getpid())
+        tuning = arr.autotune([frames[i] for i in order], [crops[i] for i in order] if crops else None,
+                              cache_path=cache)
+        try:
+            os.remove(cache)
+        except OSError:
+            pass
+        arr.sync()
     if args.timing_events != "none":
         arr.profile(True, pass_b_only=args.timing_events == "pass_b")
     order = [(t_sub[0] + j) % ring for j in range(ring)]
@@ -452,6 +465,9 @@ def run_ours(args):
         outs = [[torch.empty((c.height, opitch), dtype=torch.uint8).pin_memory() for c in wl.cams]
                 for _ in range(2)]
         arr2 = rt.CameraArray(wl.cams, stream=stream, **array_kwargs(args, wl))
+        if tuning:
+            arr2.set_tuning(**{k: tuning[k] for k in ("pass_b_threads", "pass_b_ctas_per_sm", "pass_a_rows",
+                                                      "pass_a_threads", "crop_threads", "crop_grid")})
         for i in range(3):
             arr2.submit_frames_host(host[i % nh], i, crops[i % ring] if crops else (), rgb_out=outs[i % 2],
                                     rgb_out_pitch=opitch)
@@ -510,6 +526,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": K * launches_per_set,
             "clocks": ck,
+            "tuning": tuning,
             "surrogate": sur,
         }
         print(json.dumps(line), flush=True)

@@ -233,6 +233,46 @@ rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y
  * submitted in between broke the ring's slot alignment (a multiple of 6). */
 rt_status rt_launch_sequence(rt_handle *h);
 
+/* Launch shapes of the per-frame-set kernels.  Throughput depends on them
+ * (how many pass B threads per CTA, how many CTAs per SM, how the band
+ * statistics and the crops are cut into CTAs) and on how they share the SMs
+ * when they overlap, so rt_autotune measures them on the array itself. */
+typedef struct {
+    int32_t pass_b_threads;      /* threads per pass B CTA, 64..512, a multiple of 32 */
+    int32_t pass_b_ctas_per_sm;  /* 1 or 2 (the thumbnail variant always runs 1) */
+    int32_t pass_a_rows;         /* rows per band-statistics work item, 8..1024 */
+    int32_t pass_a_threads;      /* threads per band-statistics CTA: 64, 128 or 256 */
+    int32_t crop_threads;        /* threads per crop CTA: 128 or 256 */
+    int32_t crop_grid;           /* at most this many CTAs per crop window, 1..4096 */
+    double step_us;              /* rt_autotune: measured time per frame set of this shape */
+    int32_t from_cache;          /* rt_autotune: 1 if the shape came from the cache file */
+    int32_t candidates;          /* rt_autotune: shapes timed (0 when cached) */
+} rt_tuning;
+
+/* Pick the launch shapes by timing candidates on n_sets frame sets of the
+ * caller (n_sets a positive multiple of 6; planes and crops laid out as for
+ * rt_capture_sequence): pass B's shape first, then the band statistics',
+ * then the crops', each with the best of the earlier ones fixed; every
+ * candidate is captured as a graph of the n_sets frame sets and timed over
+ * three launches with CUDA events.  cache_path (may be NULL): a JSON file
+ * mapping "device|SMs|array configuration" keys to shapes; a hit is applied
+ * without timing, a miss is timed and written back (the file is created or
+ * rewritten; other keys are kept).  The sequence state (smoothing state,
+ * motion reference, restart flag) is restored afterwards; outputs of earlier
+ * frame sets are overwritten and a captured sequence is dropped (capture
+ * again).  out (may be NULL) receives the chosen shape.  Errors: as
+ * rt_capture_sequence, RT_ERR_INVALID for a bad n_sets. */
+rt_status rt_autotune(rt_handle *h, int32_t n_sets, const void *const *y_planes, const void *const *uv_planes,
+                      const rt_crop *crops, const int32_t *n_crops, const char *cache_path, rt_tuning *out);
+
+/* The launch shapes in use (step_us, from_cache, candidates as left by the
+ * last rt_autotune, else 0). */
+rt_status rt_get_tuning(rt_handle *h, rt_tuning *out);
+
+/* Use the given launch shapes (validated as documented on rt_tuning; the
+ * informational fields are ignored).  Drops a captured sequence. */
+rt_status rt_set_tuning(rt_handle *h, const rt_tuning *t);
+
 /* Per-pass device times, from CUDA events the library records around its
  * kernels when profiling is on.  rt_profile(h, RT_PROFILE_ALL) starts
  * collecting around every pass, rt_profile(h, RT_PROFILE_PASS_B) around the

@@ -121,13 +121,13 @@ __global__ void __launch_bounds__(256) crops_kernel(const ArrayGeom g, const Cro
 
 }  // namespace
 
-cudaError_t launch_crops(const ArrayGeom &g, const CropArgs &a, cudaStream_t s)
+cudaError_t launch_crops(const ArrayGeom &g, const CropArgs &a, int threads, int max_grid, cudaStream_t s)
 {
     if (a.n <= 0) return cudaSuccess;
     const int pairs = a.S * ((a.S + 1) / 2);
-    const int per = (pairs + 255) / 256;
-    dim3 grid(per < 64 ? per : 64, a.n);
-    crops_kernel<<<grid, 256, 0, s>>>(g, a);
+    const int per = (pairs + threads - 1) / threads;
+    dim3 grid(per < max_grid ? per : max_grid, a.n);
+    crops_kernel<<<grid, threads, 0, s>>>(g, a);
     return cudaGetLastError();
 }
 

@@ -406,10 +406,8 @@ template <int FIT, bool STATS, bool THUMBS>
 cudaError_t launch_one(const ArrayGeom &g, const PassBArgs &a, int grid, int threads, cudaStream_t s)
 {
     const size_t smem = (size_t)((STATS ? kHistWords : 0) + (THUMBS ? kThumbWords : 0)) * 4;
-    // the thumbnail variant is compiled for at most 512 threads per CTA and
-    // its shared memory leaves room for one CTA per SM
+    // the thumbnail variant is compiled for at most 512 threads per CTA
     if (THUMBS && threads > 512) threads = 512;
-    if (THUMBS && STATS && grid >= RT_PASS_B_CTAS_PER_SM) grid /= RT_PASS_B_CTAS_PER_SM;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(threads);

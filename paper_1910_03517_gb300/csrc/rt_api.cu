@@ -91,6 +91,7 @@ struct rt_handle {
     size_t stage_bytes = 0;
     // events
     cudaEvent_t ev_user = nullptr, ev_in = nullptr, ev_tmp = nullptr;
+    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;   // autotuner timing
     cudaEvent_t ev_a[kEvRing] = {}, ev_solved[kEvRing] = {}, ev_done[kEvRing] = {}, ev_out[kEvRing] = {};
     bool launched[kEvRing] = {}, out_launched[kEvRing] = {};
     int64_t t = 0;                 // frame sets submitted
@@ -113,10 +114,10 @@ struct rt_handle {
     size_t cap_crops_n = 0;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_mark = nullptr;
     bool prof_branch[3] = {false, false, false};   // the capture in progress used s_prof[i]
-    // pass B launch shape
-    // one pass-B CTA per SM: 896 x 64 registers leave room for pass A and the
-    // solve of the next frame set to run beside it
-    int pb_grid = 0, pb_threads = RT_PASS_B_RUN_THREADS;
+    // launch shapes (rt_autotune / rt_set_tuning)
+    int pb_grid = 0, pb_threads = RT_PASS_B_RUN_THREADS, pb_ctas = RT_PASS_B_CTAS_PER_SM;
+    int pa_rows = kStripRows, pa_threads = 64, crop_threads = 256, crop_grid = 64;
+    rt_tuning tuned{};
     size_t pb_smem = 0;
     std::string err;
     size_t n_maps = 0;             // K*2*B*3*2
@@ -171,6 +172,33 @@ rt_status dalloc(rt_handle *h, T **p, size_t n)
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
     e = cudaMemset(*p, 0, n * sizeof(T));
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset");
+    return RT_OK;
+}
+
+// Band-statistics work items: (camera, side, block) rows split into chunks
+// of h->pa_rows rows (the device table is rebuilt when the shape changes).
+rt_status build_items(rt_handle *h)
+{
+    const int K = h->p.num_cameras, B = h->p.num_blocks;
+    std::vector<StripItem> items;
+    for (int k = 0; k < K; ++k)
+        for (int side = 0; side < 2; ++side)
+            for (int j = 0; j < B; ++j) {
+                const int H = h->cams[k].height;
+                const int r0 = (int)(((long long)j * H) / B), r1 = (int)(((long long)(j + 1) * H) / B);
+                for (int r = r0; r < r1; r += h->pa_rows) {
+                    StripItem it;
+                    it.cam = (int16_t)k; it.side = (int16_t)side; it.block = (int16_t)j; it.pad = 0;
+                    it.row0 = r; it.row1 = std::min(r1, r + h->pa_rows);
+                    items.push_back(it);
+                }
+            }
+    if (h->items) cudaFree(h->items);
+    h->items = nullptr;
+    h->n_items = (int)items.size();
+    rt_status s = dalloc(h, &h->items, items.size());
+    if (s != RT_OK) return s;
+    RT_CUDA(h, cudaMemcpy(h->items, items.data(), items.size() * sizeof(StripItem), cudaMemcpyHostToDevice));
     return RT_OK;
 }
 
@@ -265,7 +293,7 @@ void free_all(rt_handle *h)
     if (h->graph) cudaGraphDestroy(h->graph);
     F(h->cap_crops);
     for (auto e : h->ev_pool) cudaEventDestroy(e);
-    cudaEvent_t ee[] = {h->ev_user, h->ev_in, h->ev_tmp, h->ev_fork, h->ev_join, h->ev_mark};
+    cudaEvent_t ee[] = {h->ev_user, h->ev_in, h->ev_tmp, h->ev_fork, h->ev_join, h->ev_mark, h->ev_t0, h->ev_t1};
     for (auto e : ee) if (e) cudaEventDestroy(e);
     for (int i = 0; i < kEvRing; ++i) {
         if (h->ev_a[i]) cudaEventDestroy(h->ev_a[i]);
@@ -295,6 +323,8 @@ rt_status setup(rt_handle *h)
     RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_mark, cudaEventDisableTiming));
+    RT_CUDA(h, cudaEventCreate(&h->ev_t0));
+    RT_CUDA(h, cudaEventCreate(&h->ev_t1));
     for (int i = 0; i < kEvRing; ++i) {
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_a[i], cudaEventDisableTiming));
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_solved[i], cudaEventDisableTiming));
@@ -378,25 +408,8 @@ rt_status setup(rt_handle *h)
         RT_CUDA(h, cudaMemcpy(h->ramp, rmp.data(), rmp.size() * 4, cudaMemcpyHostToDevice));
         for (int k = 0; k < K; ++k) g.cam[k].ramp = h->ramp + roff[k];
     }
-    // pass A work items: (camera, side, block) rows split into chunks
-    {
-        std::vector<StripItem> items;
-        for (int k = 0; k < K; ++k)
-            for (int side = 0; side < 2; ++side)
-                for (int j = 0; j < B; ++j) {
-                    const int H = h->cams[k].height;
-                    const int r0 = (int)(((long long)j * H) / B), r1 = (int)(((long long)(j + 1) * H) / B);
-                    for (int r = r0; r < r1; r += kStripRows) {
-                        StripItem it;
-                        it.cam = (int16_t)k; it.side = (int16_t)side; it.block = (int16_t)j; it.pad = 0;
-                        it.row0 = r; it.row1 = std::min(r1, r + kStripRows);
-                        items.push_back(it);
-                    }
-                }
-        h->n_items = (int)items.size();
-        if ((s = dalloc(h, &h->items, items.size())) != RT_OK) return s;
-        RT_CUDA(h, cudaMemcpy(h->items, items.data(), items.size() * sizeof(StripItem), cudaMemcpyHostToDevice));
-    }
+    // pass A work items
+    if ((s = build_items(h)) != RT_OK) return s;
     // seam chains
     {
         std::vector<int> groups;
@@ -430,7 +443,7 @@ rt_status setup(rt_handle *h)
     }
     // pass B launch shape: a persistent grid of all resident CTAs
     RT_CUDA(h, pass_b_prepare(h->pb_threads, &h->pb_smem));
-    h->pb_grid = h->sm_count * RT_PASS_B_CTAS_PER_SM;
+    h->pb_grid = h->sm_count * h->pb_ctas;
     RT_CUDA(h, cudaDeviceSynchronize());
     return RT_OK;
 }
@@ -545,7 +558,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     const size_t nb = (size_t)K * 2 * p.num_blocks;
     pa.clear_u32 = h->strip_hist[ss_next]; pa.clear_u32_n = nb * 768 + nb * 3;
     pa.clear_u64 = h->strip_sum[ss_next]; pa.clear_u64_n = nb * 3 * 2;
-    RT_CUDA(h, launch_pass_a(g, pa, 64, h->s_stats));
+    RT_CUDA(h, launch_pass_a(g, pa, h->pa_threads, h->s_stats));
     if (prof_chain) RT_CUDA(h, prof_record(h, pe.a1, h->s_stats));
     RT_CUDA(h, cudaEventRecord(h->ev_a[ev], h->s_stats));
     RT_CUDA(h, cudaStreamWaitEvent(h->s_solve, h->ev_a[ev], 0));
@@ -589,7 +602,10 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     if (fh) { pb.clear_a = h->frame_hist[par ^ 1]; pb.clear_a_n = (uint32_t)K * 768; }
     if (th) { pb.clear_b = h->thumbs[par ^ 1]; pb.clear_b_n = (uint32_t)K * 3 * RT_THUMB_H * RT_THUMB_W; }
     if (prof) RT_CUDA(h, prof_record(h, pe.b0, h->s_main));
-    RT_CUDA(h, launch_pass_b(g, pb, h->pb_grid, h->pb_threads, h->pb_smem, h->s_main));
+    // the thumbnail variant with frame statistics needs the shared memory of
+    // one CTA per SM
+    const int pb_grid = (fh && th) ? h->sm_count : h->pb_grid;
+    RT_CUDA(h, launch_pass_b(g, pb, pb_grid, h->pb_threads, h->pb_smem, h->s_main));
     if (prof) RT_CUDA(h, prof_record(h, pe.b1, h->s_main));
     if (n_crops > 0) {
         const rt_crop *table = crop_table;
@@ -607,7 +623,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
         }
         CropArgs ca{};
         ca.crops = table; ca.n = n_crops; ca.S = p.crop_size; ca.out = h->crops[par];
-        RT_CUDA(h, launch_crops(g, ca, h->s_main));
+        RT_CUDA(h, launch_crops(g, ca, h->crop_threads, h->crop_grid, h->s_main));
         if (prof) RT_CUDA(h, prof_record(h, pe.c1, h->s_main));
     }
     if (prof) {
@@ -1025,6 +1041,309 @@ rt_status rt_launch_sequence(rt_handle *h)
     h->restart = false;
     h->last_was_graph = true;
     h->graph_launched = true;
+    return RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch shapes and the autotuner
+// ---------------------------------------------------------------------------
+
+namespace {
+
+rt_status check_shape(rt_handle *h, const rt_tuning &t)
+{
+    if (t.pass_b_threads < 64 || t.pass_b_threads > RT_PASS_B_THREADS || t.pass_b_threads % 32)
+        return fail(h, RT_ERR_INVALID, "pass_b_threads must be a multiple of 32 in 64..512");
+    if (t.pass_b_ctas_per_sm != 1 && t.pass_b_ctas_per_sm != 2) return fail(h, RT_ERR_INVALID, "pass_b_ctas_per_sm: 1 or 2");
+    if (t.pass_a_rows < 8 || t.pass_a_rows > 1024) return fail(h, RT_ERR_INVALID, "pass_a_rows must be in 8..1024");
+    if (t.pass_a_threads != 64 && t.pass_a_threads != 128 && t.pass_a_threads != 256)
+        return fail(h, RT_ERR_INVALID, "pass_a_threads: 64, 128 or 256");
+    if (t.crop_threads != 128 && t.crop_threads != 256) return fail(h, RT_ERR_INVALID, "crop_threads: 128 or 256");
+    if (t.crop_grid < 1 || t.crop_grid > 4096) return fail(h, RT_ERR_INVALID, "crop_grid must be in 1..4096");
+    return RT_OK;
+}
+
+void drop_sequence(rt_handle *h)
+{
+    if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    h->cap_n = 0;
+}
+
+rt_status apply_shape(rt_handle *h, const rt_tuning &t)
+{
+    rt_status s = check_shape(h, t);
+    if (s != RT_OK) return s;
+    if ((s = rt_sync(h, -1)) != RT_OK) return s;
+    drop_sequence(h);
+    h->pb_threads = t.pass_b_threads;
+    h->pb_ctas = t.pass_b_ctas_per_sm;
+    h->pb_grid = h->sm_count * h->pb_ctas;
+    h->pa_threads = t.pass_a_threads;
+    h->crop_threads = t.crop_threads;
+    h->crop_grid = t.crop_grid;
+    if (t.pass_a_rows != h->pa_rows) {
+        h->pa_rows = t.pass_a_rows;
+        if ((s = build_items(h)) != RT_OK) return s;
+    }
+    return RT_OK;
+}
+
+rt_tuning current_shape(const rt_handle *h)
+{
+    rt_tuning t = h->tuned;
+    t.pass_b_threads = h->pb_threads;
+    t.pass_b_ctas_per_sm = h->pb_ctas;
+    t.pass_a_rows = h->pa_rows;
+    t.pass_a_threads = h->pa_threads;
+    t.crop_threads = h->crop_threads;
+    t.crop_grid = h->crop_grid;
+    return t;
+}
+
+// Cache key: the device, its SM count and everything about the array that
+// changes the work of a frame set.
+std::string tuning_key(const rt_handle *h)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, h->dev);
+    std::string k;
+    for (const char *c = prop.name; *c; ++c) k += (*c == '"' || *c == '\\' || *c == '|') ? '_' : *c;
+    char buf[96];
+    snprintf(buf, sizeof buf, "|sm%d|", h->sm_count);
+    k += buf;
+    for (const rt_camera_desc &c : h->cams) {
+        snprintf(buf, sizeof buf, "%dx%d%s,", c.width, c.height, c.format == RT_NV12 ? "n" : "m");
+        k += buf;
+    }
+    const rt_array_params &p = h->p;
+    snprintf(buf, sizeof buf, "|S%d|B%d|fit%d|sched%d|topo%d|flags%d|crops%dx%d", p.strip_width, p.num_blocks,
+             p.fit_mode, p.schedule, p.topology, p.flags, p.max_crops, p.crop_size);
+    k += buf;
+    return k;
+}
+
+// The cache file: a JSON object, one entry per line,
+//   "key": {"pass_b_threads": 384, ..., "step_us": 32.7},
+bool read_cache(const char *path, std::vector<std::pair<std::string, std::string>> &entries)
+{
+    entries.clear();
+    FILE *f = fopen(path, "rb");
+    if (!f) return false;
+    std::string line;
+    int c;
+    auto flush = [&]() {
+        size_t q0 = line.find('"');
+        size_t q1 = q0 == std::string::npos ? q0 : line.find('"', q0 + 1);
+        size_t b0 = q1 == std::string::npos ? q1 : line.find('{', q1);
+        size_t b1 = b0 == std::string::npos ? b0 : line.find('}', b0);
+        if (b1 != std::string::npos) entries.emplace_back(line.substr(q0 + 1, q1 - q0 - 1), line.substr(b0, b1 - b0 + 1));
+        line.clear();
+    };
+    while ((c = fgetc(f)) != EOF) {
+        if (c == '\n') flush();
+        else line += (char)c;
+    }
+    flush();
+    fclose(f);
+    return true;
+}
+
+bool field(const std::string &obj, const char *name, double *v)
+{
+    const std::string pat = std::string("\"") + name + "\":";
+    const size_t at = obj.find(pat);
+    if (at == std::string::npos) return false;
+    char *end = nullptr;
+    const char *p = obj.c_str() + at + pat.size();
+    *v = strtod(p, &end);
+    return end != p;
+}
+
+bool parse_shape(const std::string &obj, rt_tuning *t)
+{
+    double v[7];
+    const char *names[7] = {"pass_b_threads", "pass_b_ctas_per_sm", "pass_a_rows", "pass_a_threads", "crop_threads",
+                            "crop_grid", "step_us"};
+    for (int i = 0; i < 7; ++i)
+        if (!field(obj, names[i], &v[i])) return false;
+    t->pass_b_threads = (int32_t)v[0]; t->pass_b_ctas_per_sm = (int32_t)v[1]; t->pass_a_rows = (int32_t)v[2];
+    t->pass_a_threads = (int32_t)v[3]; t->crop_threads = (int32_t)v[4]; t->crop_grid = (int32_t)v[5];
+    t->step_us = v[6];
+    return true;
+}
+
+bool write_cache(const char *path, const std::string &key, const rt_tuning &t)
+{
+    std::vector<std::pair<std::string, std::string>> entries;
+    read_cache(path, entries);
+    char obj[512];
+    snprintf(obj, sizeof obj,
+             "{\"pass_b_threads\": %d, \"pass_b_ctas_per_sm\": %d, \"pass_a_rows\": %d, \"pass_a_threads\": %d, "
+             "\"crop_threads\": %d, \"crop_grid\": %d, \"step_us\": %.4f}",
+             t.pass_b_threads, t.pass_b_ctas_per_sm, t.pass_a_rows, t.pass_a_threads, t.crop_threads, t.crop_grid,
+             t.step_us);
+    bool found = false;
+    for (auto &e : entries)
+        if (e.first == key) { e.second = obj; found = true; }
+    if (!found) entries.emplace_back(key, obj);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return false;
+    fputs("{\n", f);
+    for (size_t i = 0; i < entries.size(); ++i)
+        fprintf(f, "  \"%s\": %s%s\n", entries[i].first.c_str(), entries[i].second.c_str(),
+                i + 1 < entries.size() ? "," : "");
+    fputs("}\n", f);
+    const bool ok = fclose(f) == 0;
+    return ok && rename(tmp.c_str(), path) == 0;
+}
+
+// Time one shape: capture the caller's frame sets as a sequence, launch it
+// twice to warm up, then the median of three rounds of four launches
+// between events; microseconds per frame set.
+rt_status time_shape(rt_handle *h, const rt_tuning &t, int32_t n_sets, const void *const *y, const void *const *uv,
+                     const rt_crop *crops, const int32_t *n_crops, double *us)
+{
+    rt_status s = apply_shape(h, t);
+    if (s != RT_OK) return s;
+    if ((s = rt_capture_sequence(h, n_sets, y, uv, crops, n_crops)) != RT_OK) return s;
+    for (int i = 0; i < 2; ++i)
+        if ((s = rt_launch_sequence(h)) != RT_OK) return s;
+    double r[3];
+    for (int round = 0; round < 3; ++round) {
+        RT_CUDA(h, cudaEventRecord(h->ev_t0, h->s_main));
+        for (int i = 0; i < 4; ++i)
+            if ((s = rt_launch_sequence(h)) != RT_OK) return s;
+        RT_CUDA(h, cudaEventRecord(h->ev_t1, h->s_main));
+        if ((s = wait_event(h, h->ev_t1, 60000)) != RT_OK) return s;
+        float ms = 0.0f;
+        RT_CUDA(h, cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
+        r[round] = 1000.0 * ms / (4.0 * n_sets);
+    }
+    std::sort(r, r + 3);
+    *us = r[1];
+    return RT_OK;
+}
+
+}  // namespace
+
+rt_status rt_get_tuning(rt_handle *h, rt_tuning *out)
+{
+    if (!h || !out) return RT_ERR_INVALID;
+    *out = current_shape(h);
+    return RT_OK;
+}
+
+rt_status rt_set_tuning(rt_handle *h, const rt_tuning *t)
+{
+    if (!h || !t) return RT_ERR_INVALID;
+    return apply_shape(h, *t);
+}
+
+rt_status rt_autotune(rt_handle *h, int32_t n_sets, const void *const *y_planes, const void *const *uv_planes,
+                      const rt_crop *crops, const int32_t *n_crops, const char *cache_path, rt_tuning *out)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (n_sets <= 0 || n_sets % 6) return fail(h, RT_ERR_INVALID, "n_sets must be a positive multiple of 6");
+    if (!y_planes) return fail(h, RT_ERR_INVALID, "y_planes is NULL");
+    const std::string key = tuning_key(h);
+    rt_status s;
+    if (cache_path) {
+        std::vector<std::pair<std::string, std::string>> entries;
+        read_cache(cache_path, entries);
+        for (auto &e : entries) {
+            rt_tuning t{};
+            if (e.first != key || !parse_shape(e.second, &t) || check_shape(h, t) != RT_OK) continue;
+            if ((s = apply_shape(h, t)) != RT_OK) return s;
+            h->tuned = t;
+            h->tuned.from_cache = 1;
+            h->tuned.candidates = 0;
+            if (out) *out = current_shape(h);
+            return RT_OK;
+        }
+    }
+    // the sequence state to restore afterwards
+    size_t len = 0;
+    if ((s = rt_save_state(h, nullptr, &len)) != RT_OK) return s;
+    std::vector<uint8_t> state(len);
+    if ((s = rt_save_state(h, state.data(), &len)) != RT_OK) return s;
+    const int64_t t_saved = h->t;
+    // the Q16 table of the last frame set (the lagged schedule applies it next)
+    std::vector<int32_t> q_saved;
+    if (t_saved > 0) {
+        q_saved.resize(h->n_maps);
+        RT_CUDA(h, cudaMemcpy(q_saved.data(), h->q16[(int)((t_saved - 1) % kQRing)], h->n_maps * 4,
+                              cudaMemcpyDeviceToHost));
+    }
+
+    bool any_crops = false;
+    for (int i = 0; n_crops && i < n_sets; ++i) any_crops = any_crops || n_crops[i] > 0;
+    rt_tuning best = current_shape(h);
+    double best_us = 1e30;
+    int tried = 0;
+    // a candidate replaces the best so far only when it is clearly faster
+    // (timings of one shape vary by a few tenths of a percent)
+    auto consider = [&](rt_tuning c) -> rt_status {
+        double us = 0.0;
+        rt_status st = time_shape(h, c, n_sets, y_planes, uv_planes, crops, n_crops, &us);
+        if (st != RT_OK) return st;
+        ++tried;
+        if (us < best_us * 0.995) { best_us = us; best = c; }
+        return RT_OK;
+    };
+    // the shape in use first
+    s = consider(best);
+    // stage 1: pass B
+    if (s == RT_OK) {
+        const rt_tuning base = best;
+        for (int ctas = 1; ctas <= 2 && s == RT_OK; ++ctas)
+            for (int thr : {256, 320, 384, 448, 512}) {
+                rt_tuning c = base;
+                c.pass_b_ctas_per_sm = ctas;
+                c.pass_b_threads = thr;
+                if ((s = consider(c)) != RT_OK) break;
+            }
+    }
+    // stage 2: band statistics
+    if (s == RT_OK) {
+        const rt_tuning base = best;
+        for (int rows : {16, 32, 64, 128})
+            for (int thr : {64, 128}) {
+                rt_tuning c = base;
+                c.pass_a_rows = rows;
+                c.pass_a_threads = thr;
+                if ((s = consider(c)) != RT_OK) break;
+            }
+    }
+    // stage 3: crops
+    if (s == RT_OK && any_crops) {
+        const rt_tuning base = best;
+        for (int thr : {128, 256})
+            for (int grid : {64, 256, 1024}) {
+                rt_tuning c = base;
+                c.crop_threads = thr;
+                c.crop_grid = grid;
+                if ((s = consider(c)) != RT_OK) break;
+            }
+    }
+    rt_status s2 = apply_shape(h, best);
+    if (s == RT_OK) s = s2;
+    // back to the sequence as it was
+    h->t = t_saved;
+    if (s == RT_OK) s = rt_load_state(h, state.data(), len);
+    if (s == RT_OK && t_saved > 0) {
+        const cudaError_t e = cudaMemcpy(h->q16[(int)((t_saved - 1) % kQRing)], q_saved.data(), h->n_maps * 4,
+                                         cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) s = cuda_fail(h, e, "cudaMemcpy");
+    }
+    if (s != RT_OK) return s;
+    best.step_us = best_us;
+    best.from_cache = 0;
+    best.candidates = tried;
+    h->tuned = best;
+    if (cache_path && !write_cache(cache_path, key, best)) return fail(h, RT_ERR_INVALID, "cannot write the tuning cache");
+    if (out) *out = current_shape(h);
     return RT_OK;
 }
 

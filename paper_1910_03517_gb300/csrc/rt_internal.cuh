@@ -151,7 +151,7 @@ cudaError_t launch_pass_b(const ArrayGeom &g, const PassBArgs &a, int grid, int 
 cudaError_t pass_b_prepare(int threads, size_t *smem_bytes);
 cudaError_t launch_pass_a(const ArrayGeom &g, const PassAArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s);
-cudaError_t launch_crops(const ArrayGeom &g, const CropArgs &a, cudaStream_t s);
+cudaError_t launch_crops(const ArrayGeom &g, const CropArgs &a, int threads, int max_grid, cudaStream_t s);
 cudaError_t launch_thumb_features(const ArrayGeom &g, const uint32_t *thumbs, void *out, cudaStream_t s);
 cudaError_t launch_surrogate_gains(const float *y, const int32_t *group_start, const int32_t *group_members,
                                    int n_groups, const double *maps_fit, double gmin, double gmax, double *maps_out,

@@ -32,7 +32,7 @@ EXPORTS = ["rt_default_params", "rt_array_config", "rt_submit_frames", "rt_submi
            "rt_get_gains", "rt_get_corrected", "rt_copy_corrected", "rt_get_crops", "rt_get_stats",
            "rt_copy_out", "rt_sync", "rt_save_state", "rt_load_state", "rt_last_error", "rt_destroy",
            "rt_stream_wait", "rt_capture_sequence", "rt_launch_sequence", "rt_profile", "rt_get_profile",
-           "rt_get_thumb_features"]
+           "rt_get_thumb_features", "rt_autotune", "rt_get_tuning", "rt_set_tuning"]
 
 c_i32, c_i64, c_dbl, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 
@@ -57,6 +57,15 @@ class Crop(ctypes.Structure):
 class ProfileReport(ctypes.Structure):
     _fields_ = [("frame_sets", c_i32), ("pass_a_ms", c_dbl), ("solve_ms", c_dbl), ("pass_b_ms", c_dbl),
                 ("crops_ms", c_dbl)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("pass_b_threads", c_i32), ("pass_b_ctas_per_sm", c_i32), ("pass_a_rows", c_i32),
+                ("pass_a_threads", c_i32), ("crop_threads", c_i32), ("crop_grid", c_i32), ("step_us", c_dbl),
+                ("from_cache", c_i32), ("candidates", c_i32)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 class StatsView(ctypes.Structure):
@@ -99,6 +108,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rt_profile.argtypes = [c_vp, c_i32]
     L.rt_get_profile.argtypes = [c_vp, ctypes.POINTER(ProfileReport), c_i32]
     L.rt_get_thumb_features.argtypes = [c_vp, c_vp, c_i32]
+    L.rt_autotune.argtypes = [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), ctypes.POINTER(Crop),
+                              ctypes.POINTER(c_i32), ctypes.c_char_p, ctypes.POINTER(Tuning)]
+    L.rt_get_tuning.argtypes = [c_vp, ctypes.POINTER(Tuning)]
+    L.rt_set_tuning.argtypes = [c_vp, ctypes.POINTER(Tuning)]
     L.rt_destroy.argtypes = [c_vp]
     L.rt_destroy.restype = None
     L.rt_check_solve_math.argtypes = [c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]
@@ -272,8 +285,7 @@ class CameraArray:
         sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         _check(self.L, self.h, self.L.rt_stream_wait(self.h, c_vp(sp)))
 
-    def capture_sequence(self, frame_sets, crops_per_set=None):
-        """Capture a graph over a fixed ring of frame sets (len a multiple of 6)."""
+    def _sequence_args(self, frame_sets, crops_per_set):
         n = len(frame_sets)
         y = (c_vp * (n * self.K))()
         uv = (c_vp * (n * self.K))()
@@ -292,9 +304,36 @@ class CameraArray:
                 flat += [Crop(*map(int, c)) for c in cl] + [Crop()] * (M - len(cl))
             cr_p = (Crop * len(flat))(*flat)
             nc_p = (c_i32 * n)(*counts)
+        return n, y, uv, cr_p, nc_p
+
+    def capture_sequence(self, frame_sets, crops_per_set=None):
+        """Capture a graph over a fixed ring of frame sets (len a multiple of 6)."""
+        n, y, uv, cr_p, nc_p = self._sequence_args(frame_sets, crops_per_set)
         st = self.L.rt_capture_sequence(self.h, n, y, uv, cr_p, nc_p)
         _check(self.L, self.h, st)
         self._captured = frame_sets
+
+    def autotune(self, frame_sets, crops_per_set=None, cache_path=None) -> Dict[str, float]:
+        """Pick the launch shapes by timing them on these frame sets (len a
+        multiple of 6); cache_path: JSON cache file (read, and written on a miss)."""
+        n, y, uv, cr_p, nc_p = self._sequence_args(frame_sets, crops_per_set)
+        t = Tuning()
+        path = cache_path.encode() if cache_path else None
+        _check(self.L, self.h, self.L.rt_autotune(self.h, n, y, uv, cr_p, nc_p, path, ctypes.byref(t)))
+        self._captured = frame_sets
+        return t.as_dict()
+
+    def get_tuning(self) -> Dict[str, float]:
+        t = Tuning()
+        _check(self.L, self.h, self.L.rt_get_tuning(self.h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = Tuning()
+        _check(self.L, self.h, self.L.rt_get_tuning(self.h, ctypes.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        _check(self.L, self.h, self.L.rt_set_tuning(self.h, ctypes.byref(t)))
 
     def launch_sequence(self):
         _check(self.L, self.h, self.L.rt_launch_sequence(self.h))
