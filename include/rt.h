@@ -103,7 +103,13 @@ typedef struct {
  *   gain_min/gain_max  clamp of gains and of affine slopes;
  *   max_crops          crops per frame set the library can hold (0 = none);
  *   crop_size          side of the square crops (>= 1 if max_crops > 0);
- *   flags              RT_FLAG_* below. */
+ *   flags              RT_FLAG_* below;
+ *   attn_window        difference attention (RT_FLAG_ATTENTION): side of the
+ *                      square windows, a multiple of 32 in 32..4096 (256);
+ *                      windows step by attn_window / 2;
+ *   attn_min_on        on-pixels (|Y_t - Y_{t-1}| > motion_threshold) a
+ *                      window needs to be proposed, >= 1 (655, 1 % of 256^2);
+ *   attn_max           proposals kept per frame set, 1..4096 (256). */
 typedef struct {
     int32_t num_cameras;
     const rt_camera_desc *cams;
@@ -113,11 +119,21 @@ typedef struct {
     double alpha, lambda, gain_min, gain_max;
     int32_t max_crops, crop_size;
     int32_t flags;
+    int32_t attn_window, attn_min_on, attn_max;
 } rt_array_params;
 
 #define RT_FLAG_FRAME_STATS 1   /* whole-frame histograms of every camera (S2 iii) */
 #define RT_FLAG_THUMBNAILS 2    /* 64x36 thumbnail cell sums of every camera (surrogate input);
                                    needs every camera at least 64 x 36 pixels */
+#define RT_FLAG_SEAM_COST 4     /* gradient-continuity cost of every seam of the corrected
+                                   output (rt_get_seam_costs); needs every camera >= 16 x 8 */
+#define RT_FLAG_ATTENTION 8     /* difference attention: window proposals from the change of
+                                   every camera's luma between frame sets (rt_get_proposals) */
+
+/* n_crops value of rt_submit_frames / rt_capture_sequence: crop this frame
+ * set's attention proposals (RT_FLAG_ATTENTION, max_crops > 0; at most
+ * min(max_crops, attn_max) of them). */
+#define RT_CROPS_FROM_PROPOSALS (-1)
 
 /* An attention window: rectangle (x0, y0, w, h) of camera cam, inside it. */
 typedef struct { int32_t cam, x0, y0, w, h; } rt_crop;
@@ -200,6 +216,35 @@ typedef struct {
     int32_t num_cameras, num_blocks;
 } rt_stats_view;
 rt_status rt_get_stats(rt_handle *h, rt_stats_view *out, int32_t timeout_ms);
+
+/* Seam quality of the last frame set's corrected output (RT_FLAG_SEAM_COST),
+ * the cost of Sec. "Quantitative", Eq. (gradientcost): both images of a seam
+ * are box-averaged over 8 x 8 pixels (rows and columns beyond a multiple of
+ * 8 dropped); on every averaged row i that both have, with columns L-1, L0
+ * the last two of the left image and R0, R1 the first two of the right,
+ *   d+_i = |(R1 - R0) - (R0 - L0)|,  d-_i = |(L-1 - L0) - (L0 - R0)|
+ * (Euclidean norm over R, G, B), and cost = mean_i (d+_i + d-_i) / 2 --
+ * whether the colour trend continues across the seam.  One entry per seam,
+ * in chain order (groups ascending, cameras by position, a ring's closing
+ * seam last in its group): left_cam[i], right_cam[i], cost[i] (FP64).  Any
+ * output array may be NULL; cap = their capacity; *n = the number of seams
+ * (RT_ERR_INVALID if it exceeds cap).  Waits at most timeout_ms. */
+rt_status rt_get_seam_costs(rt_handle *h, int32_t *left_cam, int32_t *right_cam, double *cost, int32_t cap,
+                            int32_t *n, int32_t timeout_ms);
+
+/* Difference attention of the last frame set (RT_FLAG_ATTENTION; Sec.
+ * "Attention mechanisms", the difference approach): the change map of a
+ * camera holds the pixels whose luma (NV12 Y, or the 8-bit value of a mono
+ * camera) differs from the previous frame set's by more than
+ * motion_threshold; square windows of side attn_window slide over it at
+ * stride attn_window / 2 (2 x 2 blocks of square cells of side
+ * attn_window / 2, the last row and column of cells partial, windows clipped
+ * to the frame), and every window with at least attn_min_on on-pixels is a
+ * proposal, listed camera by camera, window row by window row, left to
+ * right, at most attn_max.  The first frame set of a sequence, and the
+ * first after rt_load_state or rt_autotune, proposes nothing.  out (may be NULL) receives min(cap, count) windows; *n the
+ * count.  Waits at most timeout_ms. */
+rt_status rt_get_proposals(rt_handle *h, rt_crop *out, int32_t cap, int32_t *n, int32_t timeout_ms);
 
 /* Wait, then write the last frame set's thumbnail features into the DEVICE
  * buffer x_bf16: BF16 [K][3][36][64], cell mean / 255 - 0.5 (the learned

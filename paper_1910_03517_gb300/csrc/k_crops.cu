@@ -82,6 +82,7 @@ __device__ __forceinline__ void pixel(const uint8_t *r0, const uint8_t *r1, floa
 __global__ void __launch_bounds__(256) crops_kernel(const ArrayGeom g, const CropArgs a)
 {
     const int n = blockIdx.y;
+    if (a.count && n >= *a.count) return;
     const rt_crop cr = a.crops[n];
     const CamGeom &cg = g.cam[cr.cam];
     const int S = a.S, hp = (S + 1) >> 1;          // pixel pairs per output row

@@ -81,6 +81,20 @@ struct rt_handle {
             *cam_H = nullptr;
     int n_groups = 0;
     SolveTopo solve_topo{};
+    // seams (left camera, right camera) in chain order, and their costs
+    std::vector<int2> seam_list;
+    int2 *seams = nullptr;
+    double *seam_cost[2] = {nullptr, nullptr};
+    // difference attention
+    AttnArgs attn{};
+    uint8_t *luma_copy[2] = {nullptr, nullptr};
+    uint32_t *attn_cells = nullptr;
+    rt_crop *props[2] = {nullptr, nullptr};
+    int32_t *prop_count[2] = {nullptr, nullptr};
+    cudaStream_t s_attn = nullptr;
+    cudaEvent_t ev_attn[4] = {};
+    bool crops_from_props[2] = {false, false};
+    bool attn_valid = false;       // luma_copy of the previous frame set holds its luma
     __half *crops[2] = {nullptr, nullptr};
     rt_crop *crop_dev[2] = {nullptr, nullptr};
     rt_crop *crop_host = nullptr;          // pinned [2][max_crops]
@@ -228,7 +242,8 @@ rt_status validate(const rt_array_params *p)
     if (p->max_crops < 0 || p->max_crops > 4096) return fail(nullptr, RT_ERR_INVALID, "max_crops must be in 0..4096");
     if (p->max_crops > 0 && (p->crop_size < 1 || p->crop_size > 4096))
         return fail(nullptr, RT_ERR_INVALID, "crop_size must be in 1..4096");
-    if (p->flags & ~(RT_FLAG_FRAME_STATS | RT_FLAG_THUMBNAILS)) return fail(nullptr, RT_ERR_INVALID, "unsupported flags");
+    if (p->flags & ~(RT_FLAG_FRAME_STATS | RT_FLAG_THUMBNAILS | RT_FLAG_SEAM_COST | RT_FLAG_ATTENTION))
+        return fail(nullptr, RT_ERR_INVALID, "unsupported flags");
     unsigned long long units = 0;
     for (int k = 0; k < p->num_cameras; ++k) {
         const rt_camera_desc &c = p->cams[k];
@@ -270,6 +285,16 @@ rt_status validate(const rt_array_params *p)
         for (int k = 0; k < p->num_cameras; ++k)
             if (p->cams[k].width < RT_THUMB_W || p->cams[k].height < RT_THUMB_H)
                 return fail(nullptr, RT_ERR_INVALID, "thumbnails need cameras of at least 64 x 36 pixels");
+    if (p->flags & RT_FLAG_ATTENTION) {
+        if (p->attn_window < 32 || p->attn_window > 4096 || p->attn_window % 32)
+            return fail(nullptr, RT_ERR_INVALID, "attn_window must be a multiple of 32 in 32..4096");
+        if (p->attn_min_on < 1) return fail(nullptr, RT_ERR_INVALID, "attn_min_on must be >= 1");
+        if (p->attn_max < 1 || p->attn_max > 4096) return fail(nullptr, RT_ERR_INVALID, "attn_max must be in 1..4096");
+    }
+    if (p->flags & RT_FLAG_SEAM_COST)
+        for (int k = 0; k < p->num_cameras; ++k)
+            if (p->cams[k].width < 16 || p->cams[k].height < 8)
+                return fail(nullptr, RT_ERR_INVALID, "seam costs need cameras of at least 16 x 8 pixels");
     return RT_OK;
 }
 
@@ -283,10 +308,13 @@ void free_all(rt_handle *h)
     for (int i = 0; i < 3; ++i) { F(h->strip_hist[i]); F(h->strip_sum[i]); }
     for (int i = 0; i < kQRing; ++i) F(h->q16[i]);
     F(h->maps_new); F(h->E); F(h->q16_identity); F(h->ramp); F(h->items); F(h->group_start);
-    F(h->group_members); F(h->left_nbr); F(h->right_nbr); F(h->cam_H);
+    F(h->group_members); F(h->left_nbr); F(h->right_nbr); F(h->cam_H); F(h->seams);
+    F(h->seam_cost[0]); F(h->seam_cost[1]);
+    F(h->luma_copy[0]); F(h->luma_copy[1]); F(h->attn_cells); F(h->props[0]); F(h->props[1]);
+    F(h->prop_count[0]); F(h->prop_count[1]);
     if (h->crop_host) cudaFreeHost(h->crop_host);
     cudaStream_t ss[] = {h->s_stats, h->s_solve, h->s_main, h->s_copy, h->s_d2h,
-                         h->s_prof[0], h->s_prof[1], h->s_prof[2]};
+                         h->s_prof[0], h->s_prof[1], h->s_prof[2], h->s_attn};
     for (auto s : ss) if (s) cudaStreamDestroy(s);
     F(h->sg_x); F(h->sg_y); F(h->sg_maps); F(h->sg_err);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
@@ -300,6 +328,7 @@ void free_all(rt_handle *h)
         if (h->ev_solved[i]) cudaEventDestroy(h->ev_solved[i]);
         if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
         if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
+        if (h->ev_attn[i]) cudaEventDestroy(h->ev_attn[i]);
     }
 }
 
@@ -314,6 +343,7 @@ rt_status setup(rt_handle *h)
     RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_stats, cudaStreamNonBlocking, hi));
     RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_solve, cudaStreamNonBlocking, hi));
     RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_main, cudaStreamNonBlocking, lo));
+    RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_attn, cudaStreamNonBlocking, hi));
     RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking));
     for (int i = 0; i < 3; ++i) RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_prof[i], cudaStreamNonBlocking));
     RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_d2h, cudaStreamNonBlocking));
@@ -330,6 +360,7 @@ rt_status setup(rt_handle *h)
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_solved[i], cudaEventDisableTiming));
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming));
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming));
+        RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_attn[i], cudaEventDisableTiming));
     }
 
     // geometry, outputs
@@ -440,8 +471,56 @@ rt_status setup(rt_handle *h)
         RT_CUDA(h, cudaMemcpy(h->right_nbr, rn.data(), rn.size() * 4, cudaMemcpyHostToDevice));
         RT_CUDA(h, cudaMemcpy(h->cam_H, hh.data(), hh.size() * 4, cudaMemcpyHostToDevice));
         fill_solve_topo(h->solve_topo, K, h->n_groups, gs.data(), gm.data(), rn.data(), hh.data());
+        h->seam_list.clear();
+        for (int gi = 0; gi < h->n_groups; ++gi) {
+            const int a0 = gs[gi], a1 = gs[gi + 1];
+            for (int i = a0; i + 1 < a1; ++i) h->seam_list.push_back(make_int2(gm[i], gm[i + 1]));
+            if (h->p.topology == RT_RING && a1 - a0 >= 2) h->seam_list.push_back(make_int2(gm[a1 - 1], gm[a0]));
+        }
+        if ((h->p.flags & RT_FLAG_SEAM_COST) && !h->seam_list.empty()) {
+            if ((s = dalloc(h, &h->seams, h->seam_list.size())) != RT_OK) return s;
+            RT_CUDA(h, cudaMemcpy(h->seams, h->seam_list.data(), h->seam_list.size() * sizeof(int2),
+                                  cudaMemcpyHostToDevice));
+            for (int i = 0; i < 2; ++i)
+                if ((s = dalloc(h, &h->seam_cost[i], h->seam_list.size())) != RT_OK) return s;
+        }
     }
     // pass B launch shape: a persistent grid of all resident CTAs
+    // difference attention: luma copies, cells, proposals
+    if (p.flags & RT_FLAG_ATTENTION) {
+        AttnArgs &a = h->attn;
+        memset(&a, 0, sizeof a);
+        a.T = p.motion_threshold;
+        a.cell = p.attn_window / 2;
+        a.min_on = p.attn_min_on;
+        a.max = p.attn_max;
+        size_t copy = 0;
+        uint32_t units = 0, cells = 0, wins = 0;
+        for (int k = 0; k < K; ++k) {
+            const rt_camera_desc &c = h->cams[k];
+            const int cpr = (c.width + 15) / 16;
+            a.unit_base[k] = units;
+            units += (uint32_t)(c.height * cpr);
+            a.copy_pitch[k] = cpr * 16;
+            a.copy_off[k] = copy;
+            copy += align_up((size_t)cpr * 16 * c.height, 256);
+            a.ncx[k] = (c.width + a.cell - 1) / a.cell;
+            a.ncy[k] = (c.height + a.cell - 1) / a.cell;
+            a.cell_off[k] = cells;
+            cells += (uint32_t)(a.ncx[k] * a.ncy[k]);
+            a.win_base[k] = wins;
+            wins += (uint32_t)(std::max(a.ncx[k] - 1, 1) * std::max(a.ncy[k] - 1, 1));
+        }
+        a.unit_base[K] = units;
+        a.cell_off[K] = cells;
+        a.win_base[K] = wins;
+        for (int i = 0; i < 2; ++i) {
+            if ((s = dalloc(h, &h->luma_copy[i], copy)) != RT_OK) return s;
+            if ((s = dalloc(h, &h->props[i], (size_t)p.attn_max)) != RT_OK) return s;
+            if ((s = dalloc(h, &h->prop_count[i], 1)) != RT_OK) return s;
+        }
+        if ((s = dalloc(h, &h->attn_cells, cells)) != RT_OK) return s;
+    }
     RT_CUDA(h, pass_b_prepare(h->pb_threads, &h->pb_smem));
     h->pb_grid = h->sm_count * h->pb_ctas;
     RT_CUDA(h, cudaDeviceSynchronize());
@@ -450,6 +529,11 @@ rt_status setup(rt_handle *h)
 
 rt_status check_crops(rt_handle *h, const rt_crop *crops, int32_t n)
 {
+    if (n == RT_CROPS_FROM_PROPOSALS) {
+        if (!(h->p.flags & RT_FLAG_ATTENTION) || h->p.max_crops < 1)
+            return fail(h, RT_ERR_INVALID, "cropping proposals needs RT_FLAG_ATTENTION and max_crops > 0");
+        return RT_OK;
+    }
     if (n < 0 || n > h->p.max_crops) return fail(h, RT_ERR_INVALID, "n_crops out of range");
     if (n > 0 && !crops) return fail(h, RT_ERR_INVALID, "crops is NULL");
     for (int i = 0; i < n; ++i) {
@@ -521,6 +605,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
         }
         RT_CUDA(h, cudaStreamWaitEvent(h->s_stats, h->ev_in, 0));
         RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_in, 0));
+        if (p.flags & RT_FLAG_ATTENTION) RT_CUDA(h, cudaStreamWaitEvent(h->s_attn, h->ev_in, 0));
     }
     const int ev2 = (int)((t + kEvRing - 2) % kEvRing);
     const bool dep2 = h->capturing ? (t - 2 >= h->cap_t0) : (t >= 2 && h->launched[ev2]);
@@ -537,6 +622,21 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     }
     if (!h->capturing && t >= 2 && h->out_launched[ev2])
         RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_out[ev2], 0));
+    // difference attention on its own stream: needs only this frame set's
+    // luma and the copy of the previous one's; its proposal slot was last
+    // read by the crops of frame set t-2
+    if (p.flags & RT_FLAG_ATTENTION) {
+        if (dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_attn, h->ev_done[ev2], 0));
+        AttnArgs aa = h->attn;
+        aa.prev = (first || !h->attn_valid) ? nullptr : h->luma_copy[par ^ 1];
+        aa.cur = h->luma_copy[par];
+        aa.cells = h->attn_cells;
+        aa.out = h->props[par];
+        aa.count = h->prop_count[par];
+        RT_CUDA(h, launch_attention(g, aa, h->sm_count, h->s_attn));
+        RT_CUDA(h, cudaEventRecord(h->ev_attn[ev], h->s_attn));
+        h->attn_valid = true;
+    }
     ProfEv pe{};
     const bool prof = h->prof_on && (h->capturing || h->prof.size() < (size_t)kMaxProfiled);
     const bool prof_chain = prof && h->prof_all;   // events around pass A and the solve too
@@ -607,7 +707,18 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     const int pb_grid = (fh && th) ? h->sm_count : h->pb_grid;
     RT_CUDA(h, launch_pass_b(g, pb, pb_grid, h->pb_threads, h->pb_smem, h->s_main));
     if (prof) RT_CUDA(h, prof_record(h, pe.b1, h->s_main));
-    if (n_crops > 0) {
+    const bool from_props = n_crops == RT_CROPS_FROM_PROPOSALS;
+    if (from_props) {
+        // this frame set's proposals, as many as the device count says
+        RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_attn[ev], 0));
+        CropArgs ca{};
+        ca.crops = h->props[par];
+        ca.n = std::min(p.max_crops, p.attn_max);
+        ca.S = p.crop_size; ca.out = h->crops[par];
+        ca.count = h->prop_count[par];
+        RT_CUDA(h, launch_crops(g, ca, h->crop_threads, h->crop_grid, h->s_main));
+        if (prof) RT_CUDA(h, prof_record(h, pe.c1, h->s_main));
+    } else if (n_crops > 0) {
         const rt_crop *table = crop_table;
         if (!table) {
             rt_crop *slot = h->crop_host + (size_t)par * p.max_crops;
@@ -627,10 +738,15 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
         if (prof) RT_CUDA(h, prof_record(h, pe.c1, h->s_main));
     }
     if (prof) {
-        pe.crops = n_crops > 0;
+        pe.crops = n_crops != 0;
         (h->capturing ? h->cap_prof : h->prof).push_back(pe);
     }
-    h->n_crops[par] = n_crops;
+    h->n_crops[par] = from_props ? std::min(p.max_crops, p.attn_max) : n_crops;
+    h->crops_from_props[par] = from_props;
+    // frame set t is done when its attention is done too
+    if (p.flags & RT_FLAG_ATTENTION) RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_attn[ev], 0));
+    if (h->seams)
+        RT_CUDA(h, launch_seam_cost(g, h->seams, (int)h->seam_list.size(), h->seam_cost[par], h->s_main));
     // frame set t is done when its own statistics chain is done too: in the
     // lagged schedule pass B(t) did not wait for solve(t) (pass B(t+1) needs
     // it anyway, so this wait costs nothing)
@@ -682,6 +798,9 @@ void rt_default_params(rt_array_params *p)
     p->gain_min = 0.25;
     p->gain_max = 4.0;
     p->flags = RT_FLAG_FRAME_STATS;
+    p->attn_window = 256;
+    p->attn_min_on = 655;
+    p->attn_max = 256;
 }
 
 rt_status rt_array_config(const rt_array_params *params, void *cuda_stream, rt_handle **out)
@@ -836,6 +955,11 @@ rt_status rt_get_crops(rt_handle *h, const void **dev_fp16_nchw, int32_t *n, int
     const int par = (int)((h->t - 1) & 1);
     *dev_fp16_nchw = h->crops[par];
     *n = h->n_crops[par];
+    if (h->crops_from_props[par]) {
+        int32_t c = 0;
+        RT_CUDA(h, cudaMemcpy(&c, h->prop_count[par], 4, cudaMemcpyDeviceToHost));
+        *n = std::min(c, *n);
+    }
     return RT_OK;
 }
 
@@ -855,6 +979,43 @@ rt_status rt_get_stats(rt_handle *h, rt_stats_view *out, int32_t timeout_ms)
     out->thumbs = (h->p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[par] : nullptr;
     out->num_cameras = h->p.num_cameras;
     out->num_blocks = h->p.num_blocks;
+    return RT_OK;
+}
+
+rt_status rt_get_seam_costs(rt_handle *h, int32_t *left_cam, int32_t *right_cam, double *cost, int32_t cap,
+                            int32_t *n, int32_t timeout_ms)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (!(h->p.flags & RT_FLAG_SEAM_COST)) return fail(h, RT_ERR_STATE, "seam costs are off (RT_FLAG_SEAM_COST)");
+    if (h->t == 0) return fail(h, RT_ERR_STATE, "no frame set submitted");
+    const int ns = (int)h->seam_list.size();
+    if (n) *n = ns;
+    if (ns > cap && (left_cam || right_cam || cost)) return fail(h, RT_ERR_INVALID, "cap too small");
+    rt_status s = wait_event(h, h->ev_done[last_ev(h)], timeout_ms);
+    if (s != RT_OK) return s;
+    for (int i = 0; i < ns; ++i) {
+        if (left_cam) left_cam[i] = h->seam_list[i].x;
+        if (right_cam) right_cam[i] = h->seam_list[i].y;
+    }
+    if (cost && ns > 0)
+        RT_CUDA(h, cudaMemcpy(cost, h->seam_cost[(int)((h->t - 1) & 1)], (size_t)ns * 8, cudaMemcpyDeviceToHost));
+    return RT_OK;
+}
+
+rt_status rt_get_proposals(rt_handle *h, rt_crop *out, int32_t cap, int32_t *n, int32_t timeout_ms)
+{
+    if (!h) return RT_ERR_INVALID;
+    if (!(h->p.flags & RT_FLAG_ATTENTION)) return fail(h, RT_ERR_STATE, "attention is off (RT_FLAG_ATTENTION)");
+    if (h->t == 0) return fail(h, RT_ERR_STATE, "no frame set submitted");
+    if (cap < 0) return fail(h, RT_ERR_INVALID, "cap < 0");
+    rt_status s = wait_event(h, h->ev_done[last_ev(h)], timeout_ms);
+    if (s != RT_OK) return s;
+    const int par = (int)((h->t - 1) & 1);
+    int32_t c = 0;
+    RT_CUDA(h, cudaMemcpy(&c, h->prop_count[par], 4, cudaMemcpyDeviceToHost));
+    if (n) *n = c;
+    const int m = std::min(c, cap);
+    if (out && m > 0) RT_CUDA(h, cudaMemcpy(out, h->props[par], sizeof(rt_crop) * m, cudaMemcpyDeviceToHost));
     return RT_OK;
 }
 
@@ -970,6 +1131,7 @@ rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y
     cudaError_t e = cudaEventRecord(h->ev_fork, h->s_main);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_stats, h->ev_fork, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_solve, h->ev_fork, 0);
+    if (e == cudaSuccess && (h->p.flags & RT_FLAG_ATTENTION)) e = cudaStreamWaitEvent(h->s_attn, h->ev_fork, 0);
     if (e != cudaSuccess) st = cuda_fail(h, e, "fork");
     for (int i = 0; i < n_sets && st == RT_OK; ++i) {
         const int nc = n_crops ? n_crops[i] : 0;
@@ -982,6 +1144,8 @@ rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_main, h->ev_join, 0);
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->s_solve);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_main, h->ev_join, 0);
+        if (e == cudaSuccess && (h->p.flags & RT_FLAG_ATTENTION)) e = cudaEventRecord(h->ev_join, h->s_attn);
+        if (e == cudaSuccess && (h->p.flags & RT_FLAG_ATTENTION)) e = cudaStreamWaitEvent(h->s_main, h->ev_join, 0);
         for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
             if (!h->prof_branch[i]) continue;
             e = cudaEventRecord(h->ev_join, h->s_prof[i]);
@@ -1033,6 +1197,7 @@ rt_status rt_launch_sequence(rt_handle *h)
     for (int i = 0; i < kEvRing; ++i) {
         RT_CUDA(h, cudaEventRecord(h->ev_a[i], h->s_main));
         RT_CUDA(h, cudaEventRecord(h->ev_solved[i], h->s_main));
+        RT_CUDA(h, cudaEventRecord(h->ev_attn[i], h->s_main));
         if (i != ev) RT_CUDA(h, cudaEventRecord(h->ev_done[i], h->s_main));
         h->launched[i] = true;
         h->out_launched[i] = false;
@@ -1278,7 +1443,7 @@ rt_status rt_autotune(rt_handle *h, int32_t n_sets, const void *const *y_planes,
     }
 
     bool any_crops = false;
-    for (int i = 0; n_crops && i < n_sets; ++i) any_crops = any_crops || n_crops[i] > 0;
+    for (int i = 0; n_crops && i < n_sets; ++i) any_crops = any_crops || n_crops[i] != 0;
     rt_tuning best = current_shape(h);
     double best_us = 1e30;
     int tried = 0;
@@ -1451,6 +1616,7 @@ rt_status rt_load_state(rt_handle *h, const void *buf, size_t len)
     const int par_prev = (int)((h->t + 1) & 1);
     RT_CUDA(h, cudaMemcpy(h->luma[par_prev], b, luma_bytes, cudaMemcpyHostToDevice));
     h->restart = hdr[3] != 0;
+    h->attn_valid = false;     // the attention's full-frame luma is not part of the state
     (void)t;
     return RT_OK;
 }

@@ -139,10 +139,27 @@ struct SolveArgs {
     float xlo_f, xhi_f;
 };
 
+// Difference attention (k_attention.cu).
+struct AttnArgs {
+    const uint8_t *prev;                    // previous frame set's luma copies (nullptr: first frame set)
+    uint8_t *cur;                           // this frame set's copies
+    uint32_t *cells;                        // on-pixel counts per cell, camera k from cell_off[k]
+    rt_crop *out;                           // proposals [max]
+    int32_t *count;                         // number of proposals
+    int32_t T, cell, min_on, max;
+    uint32_t unit_base[RT_MAX_CAMERAS + 1]; // 16-byte row pieces: H * ceil(W / 16) per camera
+    uint32_t cell_off[RT_MAX_CAMERAS + 1];
+    uint32_t win_base[RT_MAX_CAMERAS + 1];  // windows max(ncx - 1, 1) * max(ncy - 1, 1) per camera
+    int32_t ncx[RT_MAX_CAMERAS], ncy[RT_MAX_CAMERAS];
+    size_t copy_off[RT_MAX_CAMERAS];
+    int32_t copy_pitch[RT_MAX_CAMERAS];     // ceil(W / 16) * 16
+};
+
 struct CropArgs {
     const rt_crop *crops;     // device copy of this frame set's windows
     int32_t n, S;
     __half *out;              // [n][3][S][S]
+    const int32_t *count;     // device count of valid windows (nullptr: all n)
 };
 
 // Launchers (each returns the launch's cudaError_t).
@@ -152,6 +169,8 @@ cudaError_t pass_b_prepare(int threads, size_t *smem_bytes);
 cudaError_t launch_pass_a(const ArrayGeom &g, const PassAArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_crops(const ArrayGeom &g, const CropArgs &a, int threads, int max_grid, cudaStream_t s);
+cudaError_t launch_seam_cost(const ArrayGeom &g, const int2 *seams, int n_seams, double *cost, cudaStream_t s);
+cudaError_t launch_attention(const ArrayGeom &g, const AttnArgs &a, int sm_count, cudaStream_t s);
 cudaError_t launch_thumb_features(const ArrayGeom &g, const uint32_t *thumbs, void *out, cudaStream_t s);
 cudaError_t launch_surrogate_gains(const float *y, const int32_t *group_start, const int32_t *group_members,
                                    int n_groups, const double *maps_fit, double gmin, double gmax, double *maps_out,

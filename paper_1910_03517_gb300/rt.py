@@ -23,6 +23,9 @@ RT_SCHED_CURRENT, RT_SCHED_LAGGED = 0, 1
 RT_BT709, RT_BT601 = 0, 1
 RT_FLAG_FRAME_STATS = 1
 RT_FLAG_THUMBNAILS = 2
+RT_FLAG_SEAM_COST = 4
+RT_FLAG_ATTENTION = 8
+RT_CROPS_FROM_PROPOSALS = -1
 RT_PROFILE_ALL = 1
 RT_PROFILE_PASS_B = 2
 RT_MAX_CAMERAS = 32
@@ -32,7 +35,7 @@ EXPORTS = ["rt_default_params", "rt_array_config", "rt_submit_frames", "rt_submi
            "rt_get_gains", "rt_get_corrected", "rt_copy_corrected", "rt_get_crops", "rt_get_stats",
            "rt_copy_out", "rt_sync", "rt_save_state", "rt_load_state", "rt_last_error", "rt_destroy",
            "rt_stream_wait", "rt_capture_sequence", "rt_launch_sequence", "rt_profile", "rt_get_profile",
-           "rt_get_thumb_features", "rt_autotune", "rt_get_tuning", "rt_set_tuning"]
+           "rt_get_thumb_features", "rt_autotune", "rt_get_tuning", "rt_set_tuning", "rt_get_seam_costs", "rt_get_proposals"]
 
 c_i32, c_i64, c_dbl, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 
@@ -47,7 +50,8 @@ class ArrayParams(ctypes.Structure):
                 ("strip_width", c_i32), ("num_blocks", c_i32), ("fit_mode", c_i32), ("schedule", c_i32),
                 ("motion_threshold", c_i32), ("min_valid", c_i32), ("color_matrix", c_i32),
                 ("alpha", c_dbl), ("lambda_", c_dbl), ("gain_min", c_dbl), ("gain_max", c_dbl),
-                ("max_crops", c_i32), ("crop_size", c_i32), ("flags", c_i32)]
+                ("max_crops", c_i32), ("crop_size", c_i32), ("flags", c_i32),
+                ("attn_window", c_i32), ("attn_min_on", c_i32), ("attn_max", c_i32)]
 
 
 class Crop(ctypes.Structure):
@@ -108,6 +112,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.rt_profile.argtypes = [c_vp, c_i32]
     L.rt_get_profile.argtypes = [c_vp, ctypes.POINTER(ProfileReport), c_i32]
     L.rt_get_thumb_features.argtypes = [c_vp, c_vp, c_i32]
+    L.rt_get_seam_costs.argtypes = [c_vp, c_vp, c_vp, c_vp, c_i32, ctypes.POINTER(c_i32), c_i32]
+    L.rt_get_proposals.argtypes = [c_vp, c_vp, c_i32, ctypes.POINTER(c_i32), c_i32]
     L.rt_autotune.argtypes = [c_vp, c_i32, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), ctypes.POINTER(Crop),
                               ctypes.POINTER(c_i32), ctypes.c_char_p, ctypes.POINTER(Tuning)]
     L.rt_get_tuning.argtypes = [c_vp, ctypes.POINTER(Tuning)]
@@ -204,6 +210,9 @@ class CameraArray:
 
     @staticmethod
     def _crops(crops):
+        """crops: a list of (cam, x0, y0, w, h), or RT_CROPS_FROM_PROPOSALS."""
+        if isinstance(crops, int):
+            return (Crop * 1)(), int(crops)
         n = len(crops)
         arr = (Crop * max(1, n))(*[Crop(*map(int, c)) for c in crops])
         return arr, n
@@ -300,6 +309,10 @@ class CameraArray:
             flat = []
             counts = []
             for cl in crops_per_set:
+                if isinstance(cl, int):            # RT_CROPS_FROM_PROPOSALS
+                    counts.append(int(cl))
+                    flat += [Crop()] * M
+                    continue
                 counts.append(len(cl))
                 flat += [Crop(*map(int, c)) for c in cl] + [Crop()] * (M - len(cl))
             cr_p = (Crop * len(flat))(*flat)
@@ -322,6 +335,26 @@ class CameraArray:
         _check(self.L, self.h, self.L.rt_autotune(self.h, n, y, uv, cr_p, nc_p, path, ctypes.byref(t)))
         self._captured = frame_sets
         return t.as_dict()
+
+    def proposals(self, timeout_ms: int = 60000):
+        """[(cam, x0, y0, w, h)] attention windows of the last frame set (RT_FLAG_ATTENTION)."""
+        n = c_i32(0)
+        cap = max(1, self.p.attn_max)
+        buf = (Crop * cap)()
+        _check(self.L, self.h, self.L.rt_get_proposals(self.h, buf, cap, ctypes.byref(n), timeout_ms))
+        return [(c.cam, c.x0, c.y0, c.w, c.h) for c in buf[:min(n.value, cap)]]
+
+    def seam_costs(self, timeout_ms: int = 60000):
+        """[(left camera, right camera, cost)] of the last frame set (RT_FLAG_SEAM_COST)."""
+        n = c_i32(0)
+        _check(self.L, self.h, self.L.rt_get_seam_costs(self.h, None, None, None, 0, ctypes.byref(n), timeout_ms))
+        m = n.value
+        lc = np.zeros(max(m, 1), np.int32)
+        rc = np.zeros(max(m, 1), np.int32)
+        co = np.zeros(max(m, 1), np.float64)
+        _check(self.L, self.h, self.L.rt_get_seam_costs(self.h, lc.ctypes.data, rc.ctypes.data, co.ctypes.data, m,
+                                                        ctypes.byref(n), timeout_ms))
+        return [(int(lc[i]), int(rc[i]), float(co[i])) for i in range(m)]
 
     def get_tuning(self) -> Dict[str, float]:
         t = Tuning()

@@ -313,6 +313,90 @@ def test_captured_ring_matches_single_submits(rt, kw):
     b.close()
 
 
+@pytest.mark.parametrize("topology", [0, 1])
+def test_seam_costs(rt, orc, topology):
+    """Eq. (gradientcost) per seam of the corrected output against the
+    oracle's FP64 cost of the oracle's own corrected images."""
+    from oracle import seamcost
+    cams = [synth.Camera(200, 100, position=0, y_pitch=208, uv_pitch=208),
+            synth.Camera(210, 120, position=1, y_pitch=224, uv_pitch=224),
+            synth.Camera(256, 96, position=2),
+            synth.Camera(160, 64, group=1, position=0), synth.Camera(176, 72, group=1, position=1)]
+    wl = synth.Workload("seam cost", cams, frames=3, seed=23, glare_cams=(1,))
+    p = _params_for_oracle(orc, topology=topology)
+    arr = rt.CameraArray(wl.cams, flags=rt.RT_FLAG_SEAM_COST, topology=topology)
+    o = orc.ArrayOracle(wl.cams, p)
+    for t in range(3):
+        fs = synth.frame_set(wl, t, device="cuda")
+        arr.submit_frames(fs, t)
+        maps, q16 = arr.get_gains()
+        r = o.step(np_frames(fs), q16_override=q16, want_frame_stats=False)
+        got = {(l, rr): c for l, rr, c in arr.seam_costs()}
+        want = {(l, rr): seamcost.seam_cost(r["corrected"][l], r["corrected"][rr]) for _, l, rr in
+                orc.seams(wl.cams, topology)}
+        assert set(got) == set(want)
+        for key, v in want.items():
+            assert abs(got[key] - v) <= 1e-12 * max(1.0, abs(v)), (t, key, got[key], v)
+    arr.close()
+
+
+def test_attention_proposals_and_their_crops(rt, orc):
+    """Difference attention (Sec. "Attention mechanisms"): the proposal list
+    equals the oracle's exactly, frame set by frame set, and the crops of the
+    proposals equal the oracle's crops of its corrected images."""
+    from oracle import attention as oat
+    cams = [synth.Camera(640, 480, position=0), synth.Camera(650, 480, position=1, y_pitch=656, uv_pitch=656),
+            synth.Camera(300, 200, fmt=synth.MONO16, bit_depth=12, group=1, y_pitch=608)]
+    wl = synth.Workload("attention", cams, frames=5, seed=31, moving_object=True)
+    kw = dict(attn_window=128, attn_min_on=150, attn_max=12)
+    arr = rt.CameraArray(wl.cams, flags=rt.RT_FLAG_ATTENTION | rt.RT_FLAG_FRAME_STATS, max_crops=8, crop_size=48,
+                         **kw)
+    p = _params_for_oracle(orc)
+    o = orc.ArrayOracle(wl.cams, p)
+    prev = None
+    seen = 0
+    for t in range(5):
+        fs = synth.frame_set(wl, t, device="cuda")
+        arr.submit_frames(fs, t, rt.RT_CROPS_FROM_PROPOSALS)
+        lum = [orc.convert(c, f)[1] for c, f in zip(wl.cams, np_frames(fs))]
+        want = [] if prev is None else oat.proposals(wl.cams, prev, lum, 24, 128, 150, 12)[0]
+        got = arr.proposals()
+        assert got == want, (t, got[:4], want[:4])
+        seen += len(got)
+        maps, q16 = arr.get_gains()
+        crops = want[:8]
+        r = o.step(np_frames(fs), crops=crops, crop_size=48, q16_override=q16, want_frame_stats=False)
+        cr = arr.get_crops().float().cpu().numpy()
+        assert cr.shape[0] == len(crops)
+        if crops:
+            assert np.abs(cr - r["crops"]).max() < 1e-3, t
+        prev = lum
+    assert seen > 0, "the moving object was proposed"
+    arr.close()
+
+
+def test_attention_in_a_captured_ring(rt):
+    wl = synth.small_pair()
+    wl.moving_object = True
+    ring = 6
+    frames = [synth.frame_set(wl, t, device="cuda") for t in range(ring + 1)]
+    kw = dict(flags=rt.RT_FLAG_ATTENTION | rt.RT_FLAG_FRAME_STATS, max_crops=4, crop_size=32, attn_window=128,
+              attn_min_on=150, attn_max=8)
+    a = rt.CameraArray(wl.cams, **kw)
+    b = rt.CameraArray(wl.cams, **kw)
+    a.submit_frames(frames[0], 0)
+    order = [1 + j for j in range(ring)]
+    a.capture_sequence([frames[i] for i in order], [rt.RT_CROPS_FROM_PROPOSALS] * ring)
+    b.submit_frames(frames[0], 0)
+    for i in order:
+        b.submit_frames(frames[i], i, rt.RT_CROPS_FROM_PROPOSALS)
+    a.launch_sequence()
+    assert a.proposals() == b.proposals()
+    assert torch.equal(a.get_crops(), b.get_crops())
+    a.close()
+    b.close()
+
+
 def test_thumbnails_and_features(rt, orc):
     run_sequence(rt, orc, synth.small_pair(), 2, thumbs=True)
     cams = [synth.Camera(72, 38, position=0, y_pitch=80, uv_pitch=80),
