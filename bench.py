@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
+    ap.add_argument("--attention", action="store_true", help="also run the difference attention (off by default)")
+    ap.add_argument("--seam-cost", action="store_true", help="also compute the per-seam cost (off by default)")
     ap.add_argument("--timing-events", default="pass_b", choices=["pass_b", "all", "none"],
                     help="CUDA events inside the timed graph: around pass B only (the roofline's "
                          "timing), around every pass, or none (no roofline timing)")
@@ -80,7 +82,12 @@ def input_bytes(wl):
 
 def array_kwargs(args, wl):
     from paper_1910_03517_gb300 import rt
-    kw = dict(flags=rt.RT_FLAG_FRAME_STATS,
+    flags = rt.RT_FLAG_FRAME_STATS
+    if getattr(args, "attention", False):
+        flags |= rt.RT_FLAG_ATTENTION
+    if getattr(args, "seam_cost", False):
+        flags |= rt.RT_FLAG_SEAM_COST
+    kw = dict(flags=flags,
               fit_mode=rt.RT_FIT_GLOBAL if args.fit == "global" else rt.RT_FIT_SEAM_AFFINE,
               num_blocks=1 if args.fit == "global" else 16,
               schedule=rt.RT_SCHED_CURRENT if args.schedule == "current" else rt.RT_SCHED_LAGGED)
@@ -90,9 +97,14 @@ def array_kwargs(args, wl):
 
 
 def config_dict(args, wl, ring_desc):
-    return {"workload": wl.name, "cameras": len(wl.cams), "pixels_per_set": wl.pixels,
-            "fit": ("per-camera gains, 1 block" if args.fit == "global" else "seam affine maps, 16 blocks"),
-            "schedule": args.schedule, "crops_per_set": wl.n_crops, "l2": ring_desc}
+    d = {"workload": wl.name, "cameras": len(wl.cams), "pixels_per_set": wl.pixels,
+         "fit": ("per-camera gains, 1 block" if args.fit == "global" else "seam affine maps, 16 blocks"),
+         "schedule": args.schedule, "crops_per_set": wl.n_crops, "l2": ring_desc}
+    if getattr(args, "attention", False):
+        d["attention"] = "difference attention on (windows 256, stride 128, >= 655 on-pixels)"
+    if getattr(args, "seam_cost", False):
+        d["seam_cost"] = "per-seam gradient cost of the corrected output"
+    return d
 
 
 # ---------------------------------------------------------------------------
@@ -453,7 +465,7 @@ def run_ours(args):
     ab = alg_bytes(wl)
     achieved = ab / (pb_ms / 1e3) / 1e9 if pb_ms > 0 else None
     traffic = ncu_traffic(args.workload)
-    launches_per_set = 3 + (1 if wl.n_crops else 0)
+    launches_per_set = 3 + (1 if wl.n_crops else 0) + (2 if args.attention else 0) + (1 if args.seam_cost else 0)
 
     # end to end through the host-buffer entry point
     e2e = None

@@ -85,14 +85,16 @@ struct rt_handle {
     std::vector<int2> seam_list;
     int2 *seams = nullptr;
     double *seam_cost[2] = {nullptr, nullptr};
+    double *seam_rows = nullptr;   // per averaged row terms [seams][seam_max_rows]
+    int seam_max_rows = 0;
     // difference attention
     AttnArgs attn{};
     uint8_t *luma_copy[2] = {nullptr, nullptr};
     uint32_t *attn_cells = nullptr;
     rt_crop *props[2] = {nullptr, nullptr};
     int32_t *prop_count[2] = {nullptr, nullptr};
-    cudaStream_t s_attn = nullptr;
-    cudaEvent_t ev_attn[4] = {};
+    cudaStream_t s_attn = nullptr, s_aux = nullptr;   // attention; seam costs
+    cudaEvent_t ev_attn[4] = {}, ev_pb[4] = {}, ev_seam[4] = {};
     bool crops_from_props[2] = {false, false};
     bool attn_valid = false;       // luma_copy of the previous frame set holds its luma
     __half *crops[2] = {nullptr, nullptr};
@@ -309,12 +311,12 @@ void free_all(rt_handle *h)
     for (int i = 0; i < kQRing; ++i) F(h->q16[i]);
     F(h->maps_new); F(h->E); F(h->q16_identity); F(h->ramp); F(h->items); F(h->group_start);
     F(h->group_members); F(h->left_nbr); F(h->right_nbr); F(h->cam_H); F(h->seams);
-    F(h->seam_cost[0]); F(h->seam_cost[1]);
+    F(h->seam_cost[0]); F(h->seam_cost[1]); F(h->seam_rows);
     F(h->luma_copy[0]); F(h->luma_copy[1]); F(h->attn_cells); F(h->props[0]); F(h->props[1]);
     F(h->prop_count[0]); F(h->prop_count[1]);
     if (h->crop_host) cudaFreeHost(h->crop_host);
     cudaStream_t ss[] = {h->s_stats, h->s_solve, h->s_main, h->s_copy, h->s_d2h,
-                         h->s_prof[0], h->s_prof[1], h->s_prof[2], h->s_attn};
+                         h->s_prof[0], h->s_prof[1], h->s_prof[2], h->s_attn, h->s_aux};
     for (auto s : ss) if (s) cudaStreamDestroy(s);
     F(h->sg_x); F(h->sg_y); F(h->sg_maps); F(h->sg_err);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
@@ -329,6 +331,8 @@ void free_all(rt_handle *h)
         if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
         if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
         if (h->ev_attn[i]) cudaEventDestroy(h->ev_attn[i]);
+        if (h->ev_pb[i]) cudaEventDestroy(h->ev_pb[i]);
+        if (h->ev_seam[i]) cudaEventDestroy(h->ev_seam[i]);
     }
 }
 
@@ -344,6 +348,7 @@ rt_status setup(rt_handle *h)
     RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_solve, cudaStreamNonBlocking, hi));
     RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_main, cudaStreamNonBlocking, lo));
     RT_CUDA(h, cudaStreamCreateWithPriority(&h->s_attn, cudaStreamNonBlocking, hi));
+    RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking));
     RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking));
     for (int i = 0; i < 3; ++i) RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_prof[i], cudaStreamNonBlocking));
     RT_CUDA(h, cudaStreamCreateWithFlags(&h->s_d2h, cudaStreamNonBlocking));
@@ -361,6 +366,8 @@ rt_status setup(rt_handle *h)
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming));
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming));
         RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_attn[i], cudaEventDisableTiming));
+        RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_pb[i], cudaEventDisableTiming));
+        RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_seam[i], cudaEventDisableTiming));
     }
 
     // geometry, outputs
@@ -483,6 +490,11 @@ rt_status setup(rt_handle *h)
                                   cudaMemcpyHostToDevice));
             for (int i = 0; i < 2; ++i)
                 if ((s = dalloc(h, &h->seam_cost[i], h->seam_list.size())) != RT_OK) return s;
+            h->seam_max_rows = 0;
+            for (const int2 &e : h->seam_list)
+                h->seam_max_rows = std::max(h->seam_max_rows, std::min(h->cams[e.x].height, h->cams[e.y].height) / 8);
+            if ((s = dalloc(h, &h->seam_rows, h->seam_list.size() * (size_t)std::max(h->seam_max_rows, 1))) != RT_OK)
+                return s;
         }
     }
     // pass B launch shape: a persistent grid of all resident CTAs
@@ -701,6 +713,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     pb.q16 = q_apply; pb.frame_hist = fh; pb.thumbs = th;
     if (fh) { pb.clear_a = h->frame_hist[par ^ 1]; pb.clear_a_n = (uint32_t)K * 768; }
     if (th) { pb.clear_b = h->thumbs[par ^ 1]; pb.clear_b_n = (uint32_t)K * 3 * RT_THUMB_H * RT_THUMB_W; }
+    if (h->seams && dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_seam[ev2], 0));
     if (prof) RT_CUDA(h, prof_record(h, pe.b0, h->s_main));
     // the thumbnail variant with frame statistics needs the shared memory of
     // one CTA per SM
@@ -745,8 +758,14 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     h->crops_from_props[par] = from_props;
     // frame set t is done when its attention is done too
     if (p.flags & RT_FLAG_ATTENTION) RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_attn[ev], 0));
-    if (h->seams)
-        RT_CUDA(h, launch_seam_cost(g, h->seams, (int)h->seam_list.size(), h->seam_cost[par], h->s_main));
+    // seam costs on their own stream, off the path from pass B(t) to pass B(t+1)
+    if (h->seams) {
+        RT_CUDA(h, cudaEventRecord(h->ev_pb[ev], h->s_main));
+        RT_CUDA(h, cudaStreamWaitEvent(h->s_aux, h->ev_pb[ev], 0));
+        RT_CUDA(h, launch_seam_cost(g, h->seams, (int)h->seam_list.size(), h->seam_max_rows, h->seam_rows,
+                                    h->seam_cost[par], h->s_aux));
+        RT_CUDA(h, cudaEventRecord(h->ev_seam[ev], h->s_aux));
+    }
     // frame set t is done when its own statistics chain is done too: in the
     // lagged schedule pass B(t) did not wait for solve(t) (pass B(t+1) needs
     // it anyway, so this wait costs nothing)
@@ -992,6 +1011,7 @@ rt_status rt_get_seam_costs(rt_handle *h, int32_t *left_cam, int32_t *right_cam,
     if (n) *n = ns;
     if (ns > cap && (left_cam || right_cam || cost)) return fail(h, RT_ERR_INVALID, "cap too small");
     rt_status s = wait_event(h, h->ev_done[last_ev(h)], timeout_ms);
+    if (s == RT_OK && h->seams) s = wait_event(h, h->ev_seam[last_ev(h)], timeout_ms);
     if (s != RT_OK) return s;
     for (int i = 0; i < ns; ++i) {
         if (left_cam) left_cam[i] = h->seam_list[i].x;
@@ -1132,6 +1152,7 @@ rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_stats, h->ev_fork, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_solve, h->ev_fork, 0);
     if (e == cudaSuccess && (h->p.flags & RT_FLAG_ATTENTION)) e = cudaStreamWaitEvent(h->s_attn, h->ev_fork, 0);
+    if (e == cudaSuccess && h->seams) e = cudaStreamWaitEvent(h->s_aux, h->ev_fork, 0);
     if (e != cudaSuccess) st = cuda_fail(h, e, "fork");
     for (int i = 0; i < n_sets && st == RT_OK; ++i) {
         const int nc = n_crops ? n_crops[i] : 0;
@@ -1146,6 +1167,8 @@ rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_main, h->ev_join, 0);
         if (e == cudaSuccess && (h->p.flags & RT_FLAG_ATTENTION)) e = cudaEventRecord(h->ev_join, h->s_attn);
         if (e == cudaSuccess && (h->p.flags & RT_FLAG_ATTENTION)) e = cudaStreamWaitEvent(h->s_main, h->ev_join, 0);
+        if (e == cudaSuccess && h->seams) e = cudaEventRecord(h->ev_join, h->s_aux);
+        if (e == cudaSuccess && h->seams) e = cudaStreamWaitEvent(h->s_main, h->ev_join, 0);
         for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
             if (!h->prof_branch[i]) continue;
             e = cudaEventRecord(h->ev_join, h->s_prof[i]);
@@ -1198,6 +1221,7 @@ rt_status rt_launch_sequence(rt_handle *h)
         RT_CUDA(h, cudaEventRecord(h->ev_a[i], h->s_main));
         RT_CUDA(h, cudaEventRecord(h->ev_solved[i], h->s_main));
         RT_CUDA(h, cudaEventRecord(h->ev_attn[i], h->s_main));
+        RT_CUDA(h, cudaEventRecord(h->ev_seam[i], h->s_main));
         if (i != ev) RT_CUDA(h, cudaEventRecord(h->ev_done[i], h->s_main));
         h->launched[i] = true;
         h->out_launched[i] = false;
@@ -1560,7 +1584,7 @@ rt_status rt_get_profile(rt_handle *h, rt_profile_report *out, int32_t timeout_m
 rt_status rt_sync(rt_handle *h, int32_t timeout_ms)
 {
     if (!h) return RT_ERR_INVALID;
-    cudaStream_t ss[] = {h->s_copy, h->s_stats, h->s_solve, h->s_main, h->s_d2h};
+    cudaStream_t ss[] = {h->s_copy, h->s_stats, h->s_solve, h->s_main, h->s_d2h, h->s_attn, h->s_aux};
     for (auto st : ss) {
         RT_CUDA(h, cudaEventRecord(h->ev_tmp, st));
         rt_status s = wait_event(h, h->ev_tmp, timeout_ms);

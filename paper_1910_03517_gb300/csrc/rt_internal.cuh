@@ -169,7 +169,8 @@ cudaError_t pass_b_prepare(int threads, size_t *smem_bytes);
 cudaError_t launch_pass_a(const ArrayGeom &g, const PassAArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_crops(const ArrayGeom &g, const CropArgs &a, int threads, int max_grid, cudaStream_t s);
-cudaError_t launch_seam_cost(const ArrayGeom &g, const int2 *seams, int n_seams, double *cost, cudaStream_t s);
+cudaError_t launch_seam_cost(const ArrayGeom &g, const int2 *seams, int n_seams, int max_rows, double *rows,
+                             double *cost, cudaStream_t s);
 cudaError_t launch_attention(const ArrayGeom &g, const AttnArgs &a, int sm_count, cudaStream_t s);
 cudaError_t launch_thumb_features(const ArrayGeom &g, const uint32_t *thumbs, void *out, cudaStream_t s);
 cudaError_t launch_surrogate_gains(const float *y, const int32_t *group_start, const int32_t *group_members,
