@@ -28,7 +28,8 @@ import numpy as np
 from . import lib
 
 NV12, MONO16 = 0, 1
-FIT_GLOBAL, FIT_SEAM_AFFINE = 0, 1
+FIT_GLOBAL, FIT_SEAM_AFFINE, FIT_QUANTILE_AFFINE = 0, 1, 2
+QUANTILES = 32                  # levels (i + 1/2) / QUANTILES of the quantile fit
 SCHED_CURRENT, SCHED_LAGGED = 0, 1
 LINEAR, RING = 0, 1
 THUMB_W, THUMB_H = 64, 36
@@ -272,6 +273,61 @@ def fit_affine(cams, n: np.ndarray, s: np.ndarray, ss: np.ndarray, p: Params) ->
     return maps
 
 
+def quantile_levels_hit(cdf_num: np.ndarray, den: int, Q: int = QUANTILES) -> np.ndarray:
+    """For i < Q, the smallest value v with cdf(v) >= (2i + 1) / (2Q), where
+    cdf(v) = cdf_num[v] / den; decided on integers: 2 Q cdf_num[v] >= (2i + 1) den."""
+    out = np.zeros(Q, np.int64)
+    for i in range(Q):
+        v = 0
+        while 2 * Q * int(cdf_num[v]) < (2 * i + 1) * den:
+            v += 1
+        out[i] = v
+    return out
+
+
+def fit_quantile_affine(cams, hist: np.ndarray, n: np.ndarray, p: Params) -> np.ndarray:
+    """A variant of the paper's affine maps (its future work asks for better
+    matching of the spectra): each side's f_c(x) = a x + b is the least-squares
+    line through the pairs (its band's quantiles, the shared spectrum's
+    quantiles) at the levels (i + 1/2) / 32.  The shared spectrum is the
+    equal-weight mixture of the two bands (CDF the mean of the two CDFs).
+    a = cov(x, y) / var(x) from exact integer sums (1 if var(x) = 0),
+    clamped; b = mean(y) - a mean(x).  Sides without a valid seam keep the
+    identity.  hist: band histograms [K, 2, B, 3, 256]."""
+    K, B, Q = len(cams), p.num_blocks, QUANTILES
+    maps = np.zeros((K, 2, B, 3, 2), np.float64)
+    maps[..., 0] = 1.0
+    for (_, kl, kr) in seams(cams, p.topology):
+        if kl == kr:
+            continue
+        for j in range(B):
+            for c in range(3):
+                nR, nL = int(n[kl, 1, j, c]), int(n[kr, 0, j, c])
+                if nR < p.min_valid or nL < p.min_valid:
+                    continue
+                cR = np.cumsum(hist[kl, 1, j, c].astype(np.int64))
+                cL = np.cumsum(hist[kr, 0, j, c].astype(np.int64))
+                xR = quantile_levels_hit(cR, nR)
+                xL = quantile_levels_hit(cL, nL)
+                # mixture: (cR / nR + cL / nL) / 2 >= (2i+1)/(2Q)  <=>  Q (cR nL + cL nR) >= (2i+1) nR nL
+                ys = np.zeros(Q, np.int64)
+                for i in range(Q):
+                    v = 0
+                    while Q * (int(cR[v]) * nL + int(cL[v]) * nR) < (2 * i + 1) * nR * nL:
+                        v += 1
+                    ys[i] = v
+                for (k, side, xs) in ((kl, 1, xR), (kr, 0, xL)):
+                    sx, sy = int(xs.sum()), int(ys.sum())
+                    sxx, sxy = int((xs * xs).sum()), int((xs * ys).sum())
+                    den = Q * sxx - sx * sx
+                    num = Q * sxy - sx * sy
+                    a = num / den if den != 0 else 1.0
+                    a = min(max(a, p.gain_min), p.gain_max)
+                    maps[k, side, j, c, 0] = a
+                    maps[k, side, j, c, 1] = (sy - a * sx) / Q
+    return maps
+
+
 def smooth(E_prev: Optional[np.ndarray], E_new: np.ndarray, alpha: float) -> np.ndarray:
     """E_blend = (1 - alpha) E_prev + alpha E_new (Eq. of the exponential
     smoothing); the first estimate initialises E."""
@@ -349,6 +405,8 @@ class ArrayOracle:
         ss = np.stack([r[2]["sumsq"] for r in res])
         if p.fit_mode == FIT_GLOBAL:
             maps_new = fit_global(cams, n, s, p)
+        elif p.fit_mode == FIT_QUANTILE_AFFINE:
+            maps_new = fit_quantile_affine(cams, np.stack([r[2]["hist"] for r in res]), n, p)
         else:
             maps_new = fit_affine(cams, n, s, ss, p)
         E_prev = self.E
