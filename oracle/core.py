@@ -139,12 +139,15 @@ def ramp_q16(x: int, W: int) -> int:
 
 
 def apply(rgb: np.ndarray, q16_cam: np.ndarray, B: int, fit_mode: int) -> np.ndarray:
-    """q16_cam: int32 [2, B, 3, 2] = {a_q, b_q} of one camera."""
+    """q16_cam: int32 [2, B, 3, 2] = {a_q, b_q} of one camera.  Per-seam-side
+    affine maps (the paper's and the quantile fit's) are applied along the
+    convex ramp; per-camera gains on the whole image."""
     H, W, _ = rgb.shape
     q = np.ascontiguousarray(q16_cam, dtype=np.int32)
     assert q.shape == (2, B, 3, 2)
     out = np.zeros_like(rgb)
-    _c().orc_apply(_p(rgb), 3 * W, W, H, B, fit_mode, _p(q), _p(out), 3 * W)
+    ramp_mode = 0 if fit_mode == FIT_GLOBAL else FIT_SEAM_AFFINE
+    _c().orc_apply(_p(rgb), 3 * W, W, H, B, ramp_mode, _p(q), _p(out), 3 * W)
     return out
 
 
