@@ -57,7 +57,7 @@ typedef enum {
 
 enum { RT_NV12 = 0, RT_MONO16 = 1 };                 /* camera pixel formats         */
 enum { RT_LINEAR = 0, RT_RING = 1 };                 /* seam topology of every chain */
-enum { RT_FIT_GLOBAL = 0, RT_FIT_SEAM_AFFINE = 1 };  /* S3 fit                       */
+enum { RT_FIT_GLOBAL = 0, RT_FIT_SEAM_AFFINE = 1, RT_FIT_QUANTILE_AFFINE = 2 };  /* S3 fit */
 enum { RT_SCHED_CURRENT = 0, RT_SCHED_LAGGED = 1 };  /* which statistics S5 applies  */
 enum { RT_BT709 = 0, RT_BT601 = 1 };                 /* S1 colour matrix             */
 
@@ -90,7 +90,12 @@ typedef struct {
  *                      a multiple of 16 (32 by default);
  *   num_blocks         B: vertical blocks of the band, 1..RT_MAX_BLOCKS
  *                      (the paper tests 16 and 64);
- *   fit_mode           RT_FIT_GLOBAL or RT_FIT_SEAM_AFFINE;
+ *   fit_mode           RT_FIT_GLOBAL, RT_FIT_SEAM_AFFINE or RT_FIT_QUANTILE_AFFINE
+ *                      (the affine map of each seam side as the least-squares
+ *                      line through (band quantile, shared-spectrum quantile)
+ *                      pairs at the levels (i + 1/2) / 32; the shared spectrum
+ *                      is the equal-weight mixture of the two bands; applied
+ *                      like RT_FIT_SEAM_AFFINE);
  *   schedule           RT_SCHED_CURRENT: a frame set is corrected with the
  *                      estimate that includes its own statistics;
  *                      RT_SCHED_LAGGED: with the estimate of the previous

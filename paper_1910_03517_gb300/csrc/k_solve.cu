@@ -328,6 +328,57 @@ const SolveTables &solve_tables()
     return t;
 }
 
+// Quantile-LS affine maps: one thread per (camera, side, block, channel).
+// One pass over the 256 bins of both bands of the seam assigns this side's
+// 32 quantiles and the mixture's 32 (every comparison on exact integers);
+// the slope is the ratio of two exact integer sums, b follows without FMA
+// contraction -- the oracle's arithmetic, operation for operation.
+constexpr int kQuantiles = 32;
+constexpr int kQuantThreads = 64;
+
+__global__ void __launch_bounds__(kQuantThreads) solve_quantile_kernel(const SolveArgs a)
+{
+    __shared__ uint8_t sx[kQuantThreads][kQuantiles], sy[kQuantThreads][kQuantiles];
+    const int n_ent = a.K * 2 * a.B * 3;
+    const int t = threadIdx.x;
+    for (int e = blockIdx.x * blockDim.x + t; e < n_ent; e += gridDim.x * blockDim.x) {
+        const int c = e % 3, j = (e / 3) % a.B, side = (e / (3 * a.B)) % 2, cam = e / (6 * a.B);
+        const int nb = side == 1 ? a.right_nbr[cam] : a.left_nbr[cam];
+        double va = 1.0, vb = 0.0;
+        if (nb >= 0 && nb != cam) {
+            const int kl = side == 1 ? cam : nb, kr = side == 1 ? nb : cam;
+            const size_t iR = ((size_t)(kl * 2 + 1) * a.B + j) * 3 + c;
+            const size_t iL = ((size_t)(kr * 2 + 0) * a.B + j) * 3 + c;
+            const long long nR = a.n[iR], nL = a.n[iL];
+            if (nR >= a.min_valid && nL >= a.min_valid) {
+                const uint32_t *hR = a.hist + iR * 256, *hL = a.hist + iL * 256;
+                const long long nS = side == 1 ? nR : nL;       // this side's band
+                long long cR = 0, cL = 0;
+                int ix = 0, iy = 0;
+                for (int v = 0; v < 256 && (ix < kQuantiles || iy < kQuantiles); ++v) {
+                    cR += hR[v];
+                    cL += hL[v];
+                    const long long cS = side == 1 ? cR : cL;
+                    while (ix < kQuantiles && 2LL * kQuantiles * cS >= (2LL * ix + 1) * nS) sx[t][ix++] = (uint8_t)v;
+                    while (iy < kQuantiles && kQuantiles * (cR * nL + cL * nR) >= (2LL * iy + 1) * nR * nL)
+                        sy[t][iy++] = (uint8_t)v;
+                }
+                long long Sx = 0, Sy = 0, Sxx = 0, Sxy = 0;
+                for (int i = 0; i < kQuantiles; ++i) {
+                    const long long x = sx[t][i], y = sy[t][i];
+                    Sx += x; Sy += y; Sxx += x * x; Sxy += x * y;
+                }
+                const long long den = kQuantiles * Sxx - Sx * Sx, num = kQuantiles * Sxy - Sx * Sy;
+                double s = den != 0 ? (double)num / (double)den : 1.0;
+                s = fmin(fmax(s, a.gmin), a.gmax);
+                va = s;
+                vb = __ddiv_rn(__dsub_rn((double)Sy, __dmul_rn(s, (double)Sx)), (double)kQuantiles);
+            }
+        }
+        smooth_store(a, (size_t)e * 2, va, vb);
+    }
+}
+
 }  // namespace
 
 void fill_solve_topo(SolveTopo &t, int K, int n_groups, const int32_t *group_start, const int32_t *group_members,
@@ -363,6 +414,9 @@ cudaError_t launch_solve(const SolveArgs &args, cudaStream_t s)
         a.xhi_f = (float)a.xhi;
         const int n_sys = a.n_groups * a.B * 3;
         solve_global_kernel<<<n_sys, 32, 0, s>>>(a);
+    } else if (args.fit_mode == RT_FIT_QUANTILE_AFFINE) {
+        const int n_ent = args.K * 2 * args.B * 3;
+        solve_quantile_kernel<<<(n_ent + kQuantThreads - 1) / kQuantThreads, kQuantThreads, 0, s>>>(args);
     } else {
         const int n_ent = args.K * 2 * args.B * 3;
         solve_affine_kernel<<<(n_ent + 63) / 64, 64, 0, s>>>(args);

@@ -227,7 +227,7 @@ rt_status validate(const rt_array_params *p)
         return fail(nullptr, RT_ERR_INVALID, "strip_width must be a positive multiple of 16");
     if (p->num_blocks < 1 || p->num_blocks > RT_MAX_BLOCKS)
         return fail(nullptr, RT_ERR_INVALID, "num_blocks must be in 1..64");
-    if (p->fit_mode != RT_FIT_GLOBAL && p->fit_mode != RT_FIT_SEAM_AFFINE)
+    if (p->fit_mode != RT_FIT_GLOBAL && p->fit_mode != RT_FIT_SEAM_AFFINE && p->fit_mode != RT_FIT_QUANTILE_AFFINE)
         return fail(nullptr, RT_ERR_INVALID, "bad fit_mode");
     if (p->schedule != RT_SCHED_CURRENT && p->schedule != RT_SCHED_LAGGED)
         return fail(nullptr, RT_ERR_INVALID, "bad schedule");
@@ -676,7 +676,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     RT_CUDA(h, cudaStreamWaitEvent(h->s_solve, h->ev_a[ev], 0));
 
     SolveArgs sa{};
-    sa.n = h->strip_n[ss]; sa.sum = h->strip_sum[ss]; sa.sumsq = h->strip_sumsq[ss];
+    sa.n = h->strip_n[ss]; sa.sum = h->strip_sum[ss]; sa.sumsq = h->strip_sumsq[ss]; sa.hist = h->strip_hist[ss];
     sa.maps_new = h->maps_new; sa.E = h->E; sa.q16 = h->q16[qs];
     sa.K = K; sa.B = p.num_blocks; sa.S = p.strip_width; sa.fit_mode = p.fit_mode; sa.min_valid = p.min_valid;
     sa.first = first ? 1 : 0; sa.alpha = p.alpha; sa.lambda = p.lambda; sa.gmin = p.gain_min; sa.gmax = p.gain_max;

@@ -117,6 +117,7 @@ void fill_solve_topo(SolveTopo &t, int K, int n_groups, const int32_t *group_sta
 
 // Solve: fit + smoothing + quantisation.
 struct SolveArgs {
+    const uint32_t *hist;      // [K][2][B][3][256] band histograms (quantile fit)
     const uint32_t *n;
     const unsigned long long *sum, *sumsq;
     double *maps_new;          // [K][2][B][3][2] this frame set's estimate

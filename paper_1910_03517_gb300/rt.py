@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "librt.so")
 RT_OK, RT_ERR_INVALID, RT_ERR_CUDA, RT_ERR_OOM, RT_ERR_NOT_READY, RT_ERR_TIMEOUT, RT_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 RT_NV12, RT_MONO16 = 0, 1
 RT_LINEAR, RT_RING = 0, 1
-RT_FIT_GLOBAL, RT_FIT_SEAM_AFFINE = 0, 1
+RT_FIT_GLOBAL, RT_FIT_SEAM_AFFINE, RT_FIT_QUANTILE_AFFINE = 0, 1, 2
 RT_SCHED_CURRENT, RT_SCHED_LAGGED = 0, 1
 RT_BT709, RT_BT601 = 0, 1
 RT_FLAG_FRAME_STATS = 1

@@ -147,6 +147,16 @@ def test_small_pair_seam_affine_16_blocks(rt, orc):
     run_sequence(rt, orc, synth.small_pair(), 8, fit_mode=1, num_blocks=16)
 
 
+def test_quantile_affine_fit(rt, orc):
+    """The quantile-LS affine maps: maps within the FP64 bar (the kernel does
+    the oracle's arithmetic operation for operation), images bit-exact."""
+    run_sequence(rt, orc, synth.small_pair(), 6, fit_mode=2, num_blocks=16)
+    wl = synth.small_pair()
+    wl.cams = [synth.Camera(640, 480, position=i) for i in range(3)]
+    wl.moving_object = True
+    run_sequence(rt, orc, wl, 4, fit_mode=2, num_blocks=4, topology=1, schedule=1, maps_rtol=1e-12)
+
+
 def test_seam_affine_64_blocks_ring_lagged(rt, orc):
     wl = synth.small_pair()
     wl.cams = [synth.Camera(640, 480, position=i) for i in range(3)]
@@ -182,7 +192,7 @@ def test_ragged_widths_uneven_groups_and_ir(rt, orc):
         synth.Camera(34, 6, group=2, position=0, y_pitch=48, uv_pitch=48),
     ]
     wl = synth.Workload("ragged", cams, frames=4, seed=12, glare_cams=(1,))
-    for kw in ({}, {"fit_mode": 1, "num_blocks": 3}, {"num_blocks": 5, "topology": 1}):
+    for kw in ({}, {"fit_mode": 1, "num_blocks": 3}, {"num_blocks": 5, "topology": 1}, {"fit_mode": 2, "num_blocks": 2}):
         run_sequence(rt, orc, wl, 4, strip_width=16, min_valid=8, crops_per_frame=0, **kw)
 
 
