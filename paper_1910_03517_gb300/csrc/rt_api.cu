@@ -911,10 +911,15 @@ rt_status rt_submit_frames_host(rt_handle *h, const void *const *y_planes, const
     // device -> host copy of the corrected images, overlapping the next frame set
     const int ev = (int)(t % kEvRing), opar = (int)(t & 1);
     RT_CUDA(h, cudaStreamWaitEvent(h->s_d2h, h->ev_done[ev], 0));
-    for (int k = 0; k < K; ++k)
-        RT_CUDA(h, cudaMemcpy2DAsync(rgb_out[k], (size_t)rgb_out_pitch, h->rgb[opar] + h->rgb_off[k],
-                                     (size_t)h->geom.cam[k].rgb_pitch, (size_t)3 * h->cams[k].width,
-                                     h->cams[k].height, cudaMemcpyDeviceToHost, h->s_d2h));
+    for (int k = 0; k < K; ++k) {
+        const size_t row = (size_t)3 * h->cams[k].width, dpitch = (size_t)h->geom.cam[k].rgb_pitch;
+        if ((size_t)rgb_out_pitch == row && dpitch == row)   // contiguous on both sides: one linear copy
+            RT_CUDA(h, cudaMemcpyAsync(rgb_out[k], h->rgb[opar] + h->rgb_off[k], row * h->cams[k].height,
+                                       cudaMemcpyDeviceToHost, h->s_d2h));
+        else
+            RT_CUDA(h, cudaMemcpy2DAsync(rgb_out[k], (size_t)rgb_out_pitch, h->rgb[opar] + h->rgb_off[k], dpitch,
+                                         row, h->cams[k].height, cudaMemcpyDeviceToHost, h->s_d2h));
+    }
     RT_CUDA(h, cudaEventRecord(h->ev_out[ev], h->s_d2h));
     h->out_launched[ev] = true;
     return RT_OK;
