@@ -146,6 +146,95 @@ def check_solve_math(a: np.ndarray, b: np.ndarray, x: np.ndarray):
     return lr, ex
 
 
+class Box(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_float), ("y0", ctypes.c_float), ("x1", ctypes.c_float), ("y1", ctypes.c_float),
+                ("score", ctypes.c_float), ("cls", c_i32)]
+
+
+TRACK_EXPORTS = ["rt_nms", "rt_tracker_create", "rt_tracker_update", "rt_tracker_objects", "rt_tracker_destroy"]
+
+
+def _load_track(L):
+    if getattr(L, "_track_ready", False):
+        return
+    L.rt_nms.argtypes = [c_vp, c_i32, ctypes.c_float, ctypes.c_float, c_vp, c_vp]
+    L.rt_nms.restype = c_i32
+    L.rt_tracker_create.argtypes = [ctypes.POINTER(c_vp), c_dbl, c_dbl, c_dbl]
+    L.rt_tracker_create.restype = c_i32
+    L.rt_tracker_update.argtypes = [c_vp, c_vp, c_i32, c_i64, c_vp]
+    L.rt_tracker_update.restype = c_i32
+    L.rt_tracker_objects.argtypes = [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i32, ctypes.POINTER(c_i32)]
+    L.rt_tracker_objects.restype = c_i32
+    L.rt_tracker_destroy.argtypes = [c_vp]
+    L.rt_tracker_destroy.restype = None
+    L._track_ready = True
+
+
+def _boxes(rows):
+    """rows of (x0, y0, x1, y1, score, cls) -> a ctypes array of rt_box."""
+    return (Box * max(1, len(rows)))(*[Box(float(r[0]), float(r[1]), float(r[2]), float(r[3]), float(r[4]),
+                                           int(r[5])) for r in rows])
+
+
+def nms(rows, score_min: float = 0.65, iou_max: float = 0.45, stream=None) -> List[int]:
+    """Indices of the boxes greedy per-category NMS keeps (rt_nms, on the GPU)."""
+    L = load()
+    _load_track(L)
+    n = len(rows)
+    keep = np.zeros(max(1, n), np.int32)
+    st = L.rt_nms(ctypes.cast(_boxes(rows), c_vp), n, score_min, iou_max, keep.ctypes.data,
+                  None if stream is None else stream.cuda_stream)
+    if st != RT_OK:
+        raise RtError(st, "rt_nms")
+    return [i for i in range(n) if keep[i]]
+
+
+class Tracker:
+    """The paper's per-category assignment tracker (rt_tracker_*, host code)."""
+
+    def __init__(self, a: float = 0.99, tol_iou: float = 0.05, tol_new: float = 0.001):
+        self.L = load()
+        _load_track(self.L)
+        h = c_vp()
+        st = self.L.rt_tracker_create(ctypes.byref(h), a, tol_iou, tol_new)
+        if st != RT_OK:
+            raise RtError(st, "rt_tracker_create")
+        self.h = h
+
+    def update(self, rows, frame: int) -> List[int]:
+        n = len(rows)
+        out = np.zeros(max(1, n), np.int32)
+        st = self.L.rt_tracker_update(self.h, ctypes.cast(_boxes(rows), c_vp), n, int(frame), out.ctypes.data)
+        if st != RT_OK:
+            raise RtError(st, "rt_tracker_update")
+        return [int(x) for x in out[:n]]
+
+    def objects(self):
+        n = c_i32(0)
+        self.L.rt_tracker_objects(self.h, None, None, None, None, None, 0, ctypes.byref(n))
+        m = n.value
+        ids, cls, hist = (np.zeros(max(1, m), np.int32) for _ in range(3))
+        frames = np.zeros(max(1, m), np.int64)
+        boxes = (Box * max(1, m))()
+        st = self.L.rt_tracker_objects(self.h, ids.ctypes.data, cls.ctypes.data, ctypes.cast(boxes, c_vp),
+                                       frames.ctypes.data, hist.ctypes.data, m, ctypes.byref(n))
+        if st != RT_OK:
+            raise RtError(st, "rt_tracker_objects")
+        return [{"id": int(ids[i]), "cls": int(cls[i]), "frame": int(frames[i]), "history": int(hist[i]),
+                 "box": (boxes[i].x0, boxes[i].y0, boxes[i].x1, boxes[i].y1)} for i in range(m)]
+
+    def close(self):
+        if self.h:
+            self.L.rt_tracker_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class RtError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("rt status %d: %s" % (status, msg))
