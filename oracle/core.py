@@ -49,6 +49,7 @@ class Params:
     lam: float = 1e-6              # ridge term of the gain fit
     gain_min: float = 0.25
     gain_max: float = 4.0
+    blend_blocks: bool = False     # convex blending of adjacent block maps
 
 
 def _p(a: np.ndarray) -> int:
@@ -348,6 +349,32 @@ def round_half_away(v: float) -> int:
     return int(r) if v >= 0 else -int(r)
 
 
+def blend_rows(q16_cam: np.ndarray, H: int, B: int) -> np.ndarray:
+    """Per-row maps of one camera from its block maps by convex combination of
+    adjacent blocks (the paper's future work proposes it for the transition
+    between the vertical blocks).  Reading: between the centres of two
+    consecutive blocks the Q16 maps are interpolated linearly, above the
+    first centre and below the last the edge block's map holds.  With doubled
+    centres C_j = r0_j + r1_j - 1 (rows [r0_j, r1_j) of block j) and Y = 2 y:
+      w = floor(65536 (Y - C_{j-1}) / (C_j - C_{j-1}))  for C_{j-1} <= Y < C_j,
+      m(y) = m_{j-1} + floor((m_j - m_{j-1}) w / 65536),
+    in integers.  q16_cam: [2, B, 3, 2] -> [2, H, 3, 2]."""
+    q = np.asarray(q16_cam, np.int64)
+    C = [(j * H) // B + ((j + 1) * H) // B - 1 for j in range(B)]
+    out = np.zeros((2, H, 3, 2), np.int64)
+    for y in range(H):
+        Y = 2 * y
+        if Y <= C[0]:
+            out[:, y] = q[:, 0]
+        elif Y >= C[B - 1]:
+            out[:, y] = q[:, B - 1]
+        else:
+            j = next(jj for jj in range(1, B) if Y < C[jj])
+            w = (65536 * (Y - C[j - 1])) // (C[j] - C[j - 1])
+            out[:, y] = q[:, j - 1] + ((q[:, j] - q[:, j - 1]) * w) // 65536
+    return out.astype(np.int32)
+
+
 def quantise(maps: np.ndarray) -> np.ndarray:
     """Q16 table: a_q = round(65536 a), b_q = round(65536 b)."""
     flat = maps.reshape(-1)
@@ -422,6 +449,9 @@ class ArrayOracle:
         q_apply = q16 if q16_override is None else np.asarray(q16_override, np.int32)
 
         def per_cam_apply(k):
+            if p.blend_blocks and B > 1:
+                H = cams[k].height
+                return apply(rgb[k], blend_rows(q_apply[k], H, B), H, p.fit_mode)
             return apply(rgb[k], q_apply[k], B, p.fit_mode)
 
         corrected = self._map(per_cam_apply, range(K))
