@@ -134,6 +134,11 @@ typedef struct {
                                    output (rt_get_seam_costs); needs every camera >= 16 x 8 */
 #define RT_FLAG_ATTENTION 8     /* difference attention: window proposals from the change of
                                    every camera's luma between frame sets (rt_get_proposals) */
+#define RT_FLAG_BLEND_BLOCKS 16 /* with num_blocks > 1: apply per-row maps that blend adjacent
+                                   blocks' maps convexly -- linear between the centres of two
+                                   consecutive blocks (in Q16 integers), the edge blocks' maps
+                                   beyond the first and last centre -- instead of switching
+                                   maps at block borders */
 
 /* n_crops value of rt_submit_frames / rt_capture_sequence: crop this frame
  * set's attention proposals (RT_FLAG_ATTENTION, max_crops > 0; at most

@@ -149,14 +149,14 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
             for (int c = 0; c < 3; ++c) rg[0].cq[c] = 32768u - rg[0].aq[c] * kMagicBits;
             rg[1] = rg[0];
         } else {
-            jr[0] = block_of_row(y0, cg.H, B);
-            jr[1] = block_of_row(y0 + 1, cg.H, B);
+            jr[0] = block_of_row(y0, cg.H, cg.nblk);
+            jr[1] = block_of_row(y0 + 1, cg.H, cg.nblk);
             rg[0] = row_gain(q16, cam, jr[0], B);
             rg[1] = (jr[1] == jr[0]) ? rg[0] : row_gain(q16, cam, jr[1], B);
         }
     } else {
-        jr[0] = block_of_row(y0, cg.H, B);
-        jr[1] = block_of_row(y0 + 1, cg.H, B);
+        jr[0] = block_of_row(y0, cg.H, cg.nblk);
+        jr[1] = block_of_row(y0 + 1, cg.H, cg.nblk);
     }
     uint32_t ow[2][12];
     uint32_t tv[THUMBS ? 2 : 1][THUMBS ? kUnitCols : 1][3];
@@ -252,7 +252,7 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
         const uint4 a = ld_stream(yp);
         const uint4 b = (FULL || nvalid > 8) ? ld_stream(yp + 16) : make_uint4(0u, 0u, 0u, 0u);
         const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        const int j = block_of_row(y0 + r, cg.H, B);
+        const int j = block_of_row(y0 + r, cg.H, cg.nblk);
         RowGain rg;
         if (FIT == RT_FIT_GLOBAL) rg = row_gain(q16, cam, j, B);
         uint32_t tv[THUMBS ? kUnitCols : 1][3];

@@ -379,7 +379,52 @@ __global__ void __launch_bounds__(kQuantThreads) solve_quantile_kernel(const Sol
     }
 }
 
+// Per-row maps by convex combination of adjacent blocks' maps: linear
+// between the centres of consecutive blocks (doubled centres
+// C_j = floor(j H / B) + floor((j + 1) H / B) - 1 keep it in integers), the
+// edge blocks' maps beyond the first and last centre:
+//   w = floor(65536 (2y - C_{j-1}) / (C_j - C_{j-1})),
+//   m(y) = m_{j-1} + floor((m_j - m_{j-1}) w / 65536).
+// One thread per (camera, side, row) writes the row's 3 x (a_q, b_q).
+__global__ void __launch_bounds__(256) blend_rows_kernel(const ArrayGeom g, const int32_t *__restrict__ q16, int B,
+                                                         int Hmax, int32_t *__restrict__ rows)
+{
+    const int total = g.K * 2 * Hmax;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int y = e % Hmax, side = (e / Hmax) % 2, cam = e / (2 * Hmax);
+        const int H = g.cam[cam].H;
+        if (y >= H) continue;
+        const int Y = 2 * y;
+        auto centre = [&](int j) {
+            return (int)(((long long)j * H) / B + ((long long)(j + 1) * H) / B - 1);
+        };
+        const int32_t *src = q16 + (size_t)(cam * 2 + side) * B * 6;
+        int32_t *dst = rows + ((size_t)(cam * 2 + side) * Hmax + y) * 6;
+        if (Y <= centre(0)) {
+            for (int i = 0; i < 6; ++i) dst[i] = src[i];
+        } else if (Y >= centre(B - 1)) {
+            for (int i = 0; i < 6; ++i) dst[i] = src[(B - 1) * 6 + i];
+        } else {
+            int j = 1;
+            while (Y >= centre(j)) ++j;
+            const int c0 = centre(j - 1), c1 = centre(j);
+            const long long w = (65536LL * (Y - c0)) / (c1 - c0);
+            for (int i = 0; i < 6; ++i) {
+                const long long m0 = src[(j - 1) * 6 + i], m1 = src[j * 6 + i];
+                dst[i] = (int32_t)(m0 + (((m1 - m0) * w) >> 16));
+            }
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_blend_rows(const ArrayGeom &g, const int32_t *q16, int B, int Hmax, int32_t *rows, cudaStream_t s)
+{
+    const int total = g.K * 2 * Hmax;
+    blend_rows_kernel<<<(total + 255) / 256, 256, 0, s>>>(g, q16, B, Hmax, rows);
+    return cudaGetLastError();
+}
 
 void fill_solve_topo(SolveTopo &t, int K, int n_groups, const int32_t *group_start, const int32_t *group_members,
                      const int32_t *right_nbr, const int32_t *cam_H)

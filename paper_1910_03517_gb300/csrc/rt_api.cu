@@ -97,6 +97,7 @@ struct rt_handle {
     cudaEvent_t ev_attn[4] = {}, ev_pb[4] = {}, ev_seam[4] = {};
     bool crops_from_props[2] = {false, false};
     bool attn_valid = false;       // luma_copy of the previous frame set holds its luma
+    int32_t *q16_rows[2] = {nullptr, nullptr};   // per-row blended maps [K][2][Hmax][3][2]
     __half *crops[2] = {nullptr, nullptr};
     rt_crop *crop_dev[2] = {nullptr, nullptr};
     rt_crop *crop_host = nullptr;          // pinned [2][max_crops]
@@ -244,7 +245,8 @@ rt_status validate(const rt_array_params *p)
     if (p->max_crops < 0 || p->max_crops > 4096) return fail(nullptr, RT_ERR_INVALID, "max_crops must be in 0..4096");
     if (p->max_crops > 0 && (p->crop_size < 1 || p->crop_size > 4096))
         return fail(nullptr, RT_ERR_INVALID, "crop_size must be in 1..4096");
-    if (p->flags & ~(RT_FLAG_FRAME_STATS | RT_FLAG_THUMBNAILS | RT_FLAG_SEAM_COST | RT_FLAG_ATTENTION))
+    if (p->flags & ~(RT_FLAG_FRAME_STATS | RT_FLAG_THUMBNAILS | RT_FLAG_SEAM_COST | RT_FLAG_ATTENTION |
+                     RT_FLAG_BLEND_BLOCKS))
         return fail(nullptr, RT_ERR_INVALID, "unsupported flags");
     unsigned long long units = 0;
     for (int k = 0; k < p->num_cameras; ++k) {
@@ -313,7 +315,7 @@ void free_all(rt_handle *h)
     F(h->group_members); F(h->left_nbr); F(h->right_nbr); F(h->cam_H); F(h->seams);
     F(h->seam_cost[0]); F(h->seam_cost[1]); F(h->seam_rows);
     F(h->luma_copy[0]); F(h->luma_copy[1]); F(h->attn_cells); F(h->props[0]); F(h->props[1]);
-    F(h->prop_count[0]); F(h->prop_count[1]);
+    F(h->prop_count[0]); F(h->prop_count[1]); F(h->q16_rows[0]); F(h->q16_rows[1]);
     if (h->crop_host) cudaFreeHost(h->crop_host);
     cudaStream_t ss[] = {h->s_stats, h->s_solve, h->s_main, h->s_copy, h->s_d2h,
                          h->s_prof[0], h->s_prof[1], h->s_prof[2], h->s_attn, h->s_aux};
@@ -386,6 +388,7 @@ rt_status setup(rt_handle *h)
         cg.rgb_pitch = (int)align_up((size_t)3 * c.width, 16);
         cg.fmt = c.format; cg.shift = c.format == RT_MONO16 ? c.bit_depth - 8 : 0;
         cg.upr = (uint32_t)((c.width + 15) / 16);
+        cg.nblk = ((p.flags & RT_FLAG_BLEND_BLOCKS) && B > 1) ? c.height : B;
         cg.unit_base = units;
         units += cg.upr * (uint32_t)(c.height / 2);
         h->rgb_off[k] = off;
@@ -498,6 +501,9 @@ rt_status setup(rt_handle *h)
         }
     }
     // pass B launch shape: a persistent grid of all resident CTAs
+    if ((p.flags & RT_FLAG_BLEND_BLOCKS) && B > 1)
+        for (int i = 0; i < 2; ++i)
+            if ((s = dalloc(h, &h->q16_rows[i], (size_t)K * 2 * h->Hmax * 6)) != RT_OK) return s;
     // difference attention: luma copies, cells, proposals
     if (p.flags & RT_FLAG_ATTENTION) {
         AttnArgs &a = h->attn;
@@ -711,6 +717,12 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     uint32_t *th = (p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[par] : nullptr;
     PassBArgs pb{};
     pb.q16 = q_apply; pb.frame_hist = fh; pb.thumbs = th;
+    if (h->q16_rows[0]) {
+        // one blended map per row: the table pass B reads has Hmax "blocks"
+        RT_CUDA(h, launch_blend_rows(g, q_apply, p.num_blocks, h->Hmax, h->q16_rows[par], h->s_main));
+        pb.q16 = h->q16_rows[par];
+        g.B = h->Hmax;
+    }
     if (fh) { pb.clear_a = h->frame_hist[par ^ 1]; pb.clear_a_n = (uint32_t)K * 768; }
     if (th) { pb.clear_b = h->thumbs[par ^ 1]; pb.clear_b_n = (uint32_t)K * 3 * RT_THUMB_H * RT_THUMB_W; }
     if (h->seams && dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_seam[ev2], 0));

@@ -41,6 +41,8 @@ struct CamGeom {
     uint8_t *rgb;           // corrected RGB24 output
     int32_t W, H, y_pitch, uv_pitch, rgb_pitch;
     int32_t fmt, shift;     // shift = bit_depth - 8 for mono
+    int32_t nblk;           // blocks of this camera's rows in the applied map table
+                            // (B; H when the table holds one map per row)
     uint32_t upr;           // units per row pair = ceil(W / 16)
     uint32_t unit_base;     // first unit of this camera in the array's unit space
     const int32_t *ramp;    // Q16 ramp weight per column (seam maps)
@@ -173,6 +175,9 @@ cudaError_t launch_crops(const ArrayGeom &g, const CropArgs &a, int threads, int
 cudaError_t launch_seam_cost(const ArrayGeom &g, const int2 *seams, int n_seams, int max_rows, double *rows,
                              double *cost, cudaStream_t s);
 cudaError_t launch_attention(const ArrayGeom &g, const AttnArgs &a, int sm_count, cudaStream_t s);
+// Per-row maps by convex blending of adjacent blocks: rows[K][2][Hmax][3][2]
+// from q16[K][2][B][3][2].
+cudaError_t launch_blend_rows(const ArrayGeom &g, const int32_t *q16, int B, int Hmax, int32_t *rows, cudaStream_t s);
 cudaError_t launch_thumb_features(const ArrayGeom &g, const uint32_t *thumbs, void *out, cudaStream_t s);
 cudaError_t launch_surrogate_gains(const float *y, const int32_t *group_start, const int32_t *group_members,
                                    int n_groups, const double *maps_fit, double gmin, double gmax, double *maps_out,

@@ -104,6 +104,7 @@ extern "C" rt_status rt_fit_gains_noalloc(const rt_camera_desc *cams, int32_t nu
         cg.W = cams[k].width; cg.H = cams[k].height;
         cg.y_pitch = cams[k].y_pitch; cg.uv_pitch = cams[k].uv_pitch;
         cg.fmt = cams[k].format; cg.shift = cams[k].format == RT_MONO16 ? cams[k].bit_depth - 8 : 0;
+        cg.nblk = B;
         if (cg.H > Hmax) Hmax = cg.H;
     }
     // band work items and seam tables (host arrays on the stack, copied in)

@@ -25,6 +25,7 @@ RT_FLAG_FRAME_STATS = 1
 RT_FLAG_THUMBNAILS = 2
 RT_FLAG_SEAM_COST = 4
 RT_FLAG_ATTENTION = 8
+RT_FLAG_BLEND_BLOCKS = 16
 RT_CROPS_FROM_PROPOSALS = -1
 RT_PROFILE_ALL = 1
 RT_PROFILE_PASS_B = 2

@@ -48,11 +48,13 @@ def _check_q16(q_gpu, q_orc, E):
 
 
 def run_sequence(rt, orc, wl, frames, crops_per_frame=0, crop_size=0, device_inputs=True,
-                 stats=True, check_images=True, thumbs=False, maps_rtol=1e-6, **kw):
+                 stats=True, check_images=True, thumbs=False, maps_rtol=1e-6, blend=False, **kw):
     """Submit `frames` frame sets to the GPU and the oracle, compare each."""
     from oracle import mlp as omlp
     p = _params_for_oracle(orc, **kw)
-    flags = (rt.RT_FLAG_FRAME_STATS if stats else 0) | (rt.RT_FLAG_THUMBNAILS if thumbs else 0)
+    p.blend_blocks = blend
+    flags = (rt.RT_FLAG_FRAME_STATS if stats else 0) | (rt.RT_FLAG_THUMBNAILS if thumbs else 0) | \
+        (rt.RT_FLAG_BLEND_BLOCKS if blend else 0)
     arr = rt.CameraArray(wl.cams, max_crops=max(crops_per_frame, 0), crop_size=max(crop_size, 0),
                          flags=flags, **kw)
     o = orc.ArrayOracle(wl.cams, p)
@@ -145,6 +147,21 @@ def test_small_pair_global(rt, orc):
 
 def test_small_pair_seam_affine_16_blocks(rt, orc):
     run_sequence(rt, orc, synth.small_pair(), 8, fit_mode=1, num_blocks=16)
+
+
+@pytest.mark.parametrize("kw", [{"num_blocks": 16}, {"fit_mode": 1, "num_blocks": 16},
+                                {"fit_mode": 2, "num_blocks": 7, "schedule": 1}])
+def test_blended_block_maps(rt, orc, kw):
+    """Convex blending of adjacent block maps: per-row maps in exact Q16
+    integers, images bit-exact to the oracle; also cameras of several heights
+    (the per-row table has the tallest camera's rows)."""
+    run_sequence(rt, orc, synth.small_pair(), 4, blend=True, **kw)
+    cams = [synth.Camera(200, 120, position=0, y_pitch=208, uv_pitch=208),
+            synth.Camera(220, 90, position=1, y_pitch=224, uv_pitch=224),
+            synth.Camera(96, 40, fmt=synth.MONO16, bit_depth=10, group=1, position=0, y_pitch=192),
+            synth.Camera(96, 64, fmt=synth.MONO16, bit_depth=10, group=1, position=1, y_pitch=192)]
+    wl = synth.Workload("blend ragged", cams, frames=3, seed=41)
+    run_sequence(rt, orc, wl, 3, blend=True, strip_width=16, min_valid=8, **kw)
 
 
 def test_quantile_affine_fit(rt, orc):
