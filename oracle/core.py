@@ -28,7 +28,8 @@ import numpy as np
 from . import lib
 
 NV12, MONO16 = 0, 1
-FIT_GLOBAL, FIT_SEAM_AFFINE, FIT_QUANTILE_AFFINE = 0, 1, 2
+FIT_GLOBAL, FIT_SEAM_AFFINE, FIT_QUANTILE_AFFINE, FIT_MATRIX = 0, 1, 2, 3
+MATRIX_RIDGE = 0.25             # added to band covariances (half an LSB of noise, squared)
 QUANTILES = 32                  # levels (i + 1/2) / QUANTILES of the quantile fit
 SCHED_CURRENT, SCHED_LAGGED = 0, 1
 LINEAR, RING = 0, 1
@@ -75,6 +76,8 @@ def _c():
         L.orc_ramp_q16.restype = ctypes.c_int32
         L.orc_apply.argtypes = [vp, i64, i32, i32, i32, i32, vp, vp, i64]
         L.orc_crop.argtypes = [vp, i64, i32, i32, i32, i32, i32, vp]
+        L.orc_strip_joint.argtypes = [vp, i64, vp, i64, vp, i64, i32, i32, i32, i32, i32, vp]
+        L.orc_apply_matrix.argtypes = [vp, i64, i32, i32, i32, vp, vp, i64]
         _C = L
     return _C
 
@@ -117,6 +120,17 @@ def strip_stats(rgb: np.ndarray, luma: np.ndarray, prev_luma: Optional[np.ndarra
     _c().orc_strip_stats(_p(rgb), 3 * W, _p(luma), W, prev_ptr, W, W, H, S, B, T,
                          _p(n), _p(s), _p(ss), _p(h))
     return {"n": n, "sum": s, "sumsq": ss, "hist": h}
+
+
+def strip_joint(rgb: np.ndarray, luma: np.ndarray, prev_luma: Optional[np.ndarray],
+                S: int, B: int, T: int) -> np.ndarray:
+    """Joint band statistics [2, B, 10] = {n, sums R G B, RR RG RB GG GB BB}
+    over pixels neither moving nor saturated in any channel."""
+    H, W, _ = rgb.shape
+    out = np.zeros((2, B, 10), np.uint64)
+    prev_ptr = None if prev_luma is None else _p(prev_luma)
+    _c().orc_strip_joint(_p(rgb), 3 * W, _p(luma), W, prev_ptr, W, W, H, S, B, T, _p(out))
+    return out
 
 
 def frame_stats(rgb: np.ndarray) -> Dict[str, np.ndarray]:
@@ -349,6 +363,66 @@ def round_half_away(v: float) -> int:
     return int(r) if v >= 0 else -int(r)
 
 
+def _sym_fn(A: np.ndarray, f) -> np.ndarray:
+    lam, V = np.linalg.eigh(A)
+    return (V * f(lam)) @ V.T
+
+
+def joint_moments(q: np.ndarray):
+    """(mean [3], covariance [3, 3] + MATRIX_RIDGE I) of joint band statistics."""
+    n = float(q[0])
+    mu = np.array([float(q[1]), float(q[2]), float(q[3])]) / n
+    S = np.array([[q[4], q[5], q[6]], [q[5], q[7], q[8]], [q[6], q[8], q[9]]], np.float64) / n
+    return mu, S - np.outer(mu, mu) + MATRIX_RIDGE * np.eye(3)
+
+
+def fit_matrix(cams, joint: np.ndarray, p: Params) -> np.ndarray:
+    """3 x 3 cross-channel maps (the paper's future work: linear maps
+    combining the three channels), the multichannel form of the paper's
+    moment matching: the shared spectrum is the equal-weight mixture of the
+    two bands (mean mu_s = (mu_L + mu_R)/2, covariance (S_L + S_R)/2 +
+    d d^T / 4, d = mu_L - mu_R); each side's M is the symmetric positive
+    definite map with M S M^T = S_s,
+        M = S^-1/2 (S^1/2 S_s S^1/2)^1/2 S^-1/2,
+    its eigenvalues clamped to [gain_min, gain_max], b = mu_s - M mu.  With
+    diagonal covariances M_cc = sqrt(S_s,cc / S_cc), the per-channel rule.
+    Covariances carry a ridge of 0.25.  joint: [K, 2, B, 10]; returns maps
+    [K, 2, B, 12] = {M row-major, b}; sides without a valid seam: identity."""
+    K, B = len(cams), p.num_blocks
+    maps = np.zeros((K, 2, B, 12), np.float64)
+    maps[..., 0] = maps[..., 4] = maps[..., 8] = 1.0
+    for (_, kl, kr) in seams(cams, p.topology):
+        if kl == kr:
+            continue
+        for j in range(B):
+            qR, qL = joint[kl, 1, j], joint[kr, 0, j]
+            if int(qR[0]) < p.min_valid or int(qL[0]) < p.min_valid:
+                continue
+            muR, SR = joint_moments(qR)
+            muL, SL = joint_moments(qL)
+            d = muL - muR
+            mus = 0.5 * (muL + muR)
+            Ss = 0.5 * (SL + SR) + 0.25 * np.outer(d, d)
+            for (k, side, mu, S) in ((kl, 1, muR, SR), (kr, 0, muL, SL)):
+                h = _sym_fn(S, np.sqrt)
+                hi = _sym_fn(S, lambda l: 1.0 / np.sqrt(l))
+                M = hi @ _sym_fn(h @ Ss @ h, np.sqrt) @ hi
+                M = _sym_fn(0.5 * (M + M.T), lambda l: np.clip(l, p.gain_min, p.gain_max))
+                maps[k, side, j, :9] = M.reshape(9)
+                maps[k, side, j, 9:] = mus - M @ mu
+    return maps
+
+
+def apply_matrix(rgb: np.ndarray, q16_cam: np.ndarray, B: int) -> np.ndarray:
+    """q16_cam: int32 [2, B, 12] of one camera (orc_apply_matrix)."""
+    H, W, _ = rgb.shape
+    q = np.ascontiguousarray(q16_cam, dtype=np.int32)
+    assert q.shape == (2, B, 12)
+    out = np.zeros_like(rgb)
+    _c().orc_apply_matrix(_p(rgb), 3 * W, W, H, B, _p(q), _p(out), 3 * W)
+    return out
+
+
 def blend_rows(q16_cam: np.ndarray, H: int, B: int) -> np.ndarray:
     """Per-row maps of one camera from its block maps by convex combination of
     adjacent blocks (the paper's future work proposes it for the transition
@@ -358,10 +432,11 @@ def blend_rows(q16_cam: np.ndarray, H: int, B: int) -> np.ndarray:
     centres C_j = r0_j + r1_j - 1 (rows [r0_j, r1_j) of block j) and Y = 2 y:
       w = floor(65536 (Y - C_{j-1}) / (C_j - C_{j-1}))  for C_{j-1} <= Y < C_j,
       m(y) = m_{j-1} + floor((m_j - m_{j-1}) w / 65536),
-    in integers.  q16_cam: [2, B, 3, 2] -> [2, H, 3, 2]."""
+    in integers, for every value of the table.  q16_cam: [2, B, ...] ->
+    [2, H, ...] ([2, B, 3, 2] affine maps, [2, B, 12] 3 x 3 maps)."""
     q = np.asarray(q16_cam, np.int64)
     C = [(j * H) // B + ((j + 1) * H) // B - 1 for j in range(B)]
-    out = np.zeros((2, H, 3, 2), np.int64)
+    out = np.zeros((2, H) + q.shape[2:], np.int64)
     for y in range(H):
         Y = 2 * y
         if Y <= C[0]:
@@ -383,7 +458,11 @@ def quantise(maps: np.ndarray) -> np.ndarray:
     return out.astype(np.int32).reshape(maps.shape)
 
 
-def identity_maps(K: int, B: int) -> np.ndarray:
+def identity_maps(K: int, B: int, fit_mode: int = FIT_GLOBAL) -> np.ndarray:
+    if fit_mode == FIT_MATRIX:
+        m = np.zeros((K, 2, B, 12), np.float64)
+        m[..., 0] = m[..., 4] = m[..., 8] = 1.0
+        return m
     m = np.zeros((K, 2, B, 3, 2), np.float64)
     m[..., 0] = 1.0
     return m
@@ -426,6 +505,9 @@ class ArrayOracle:
                              p.strip_width, B, p.motion_threshold)
             fs = frame_stats(rgb) if want_frame_stats else None
             th = thumbnail(rgb) if want_thumbs else None
+            if p.fit_mode == FIT_MATRIX:
+                st["joint"] = strip_joint(rgb, luma, None if first else self.prev_luma[k],
+                                          p.strip_width, B, p.motion_threshold)
             return rgb, luma, st, fs, th
 
         res = self._map(per_cam_stats, range(K))
@@ -437,6 +519,9 @@ class ArrayOracle:
             maps_new = fit_global(cams, n, s, p)
         elif p.fit_mode == FIT_QUANTILE_AFFINE:
             maps_new = fit_quantile_affine(cams, np.stack([r[2]["hist"] for r in res]), n, p)
+        elif p.fit_mode == FIT_MATRIX:
+            joint = np.stack([r[2]["joint"] for r in res])
+            maps_new = fit_matrix(cams, joint, p)
         else:
             maps_new = fit_affine(cams, n, s, ss, p)
         E_prev = self.E
@@ -444,15 +529,17 @@ class ArrayOracle:
         if p.schedule == SCHED_CURRENT:
             maps_used = self.E
         else:  # lagged: this frame set is corrected with the previous estimate
-            maps_used = E_prev if E_prev is not None else identity_maps(K, B)
+            maps_used = E_prev if E_prev is not None else identity_maps(K, B, p.fit_mode)
         q16 = quantise(maps_used)
         q_apply = q16 if q16_override is None else np.asarray(q16_override, np.int32)
 
         def per_cam_apply(k):
+            q, nb = q_apply[k], B
             if p.blend_blocks and B > 1:
-                H = cams[k].height
-                return apply(rgb[k], blend_rows(q_apply[k], H, B), H, p.fit_mode)
-            return apply(rgb[k], q_apply[k], B, p.fit_mode)
+                q, nb = blend_rows(q, cams[k].height, B), cams[k].height
+            if p.fit_mode == FIT_MATRIX:
+                return apply_matrix(rgb[k], q, nb)
+            return apply(rgb[k], q, nb, p.fit_mode)
 
         corrected = self._map(per_cam_apply, range(K))
         out_crops = None
@@ -467,6 +554,7 @@ class ArrayOracle:
             "frame_sum": np.stack([r[3]["sum"] for r in res]) if want_frame_stats else None,
             "frame_sumsq": np.stack([r[3]["sumsq"] for r in res]) if want_frame_stats else None,
             "thumbs": np.stack([r[4] for r in res]) if want_thumbs else None,
+            "strip_joint": joint if p.fit_mode == FIT_MATRIX else None,
             "maps_new": maps_new, "maps": maps_used, "E": self.E, "q16": q16,
             "crops": out_crops,
         }

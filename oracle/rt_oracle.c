@@ -253,3 +253,71 @@ void orc_crop(const uint8_t *rgb, int64_t rgb_pitch, int x0, int y0, int w, int 
         }
     }
 }
+
+/* Joint band statistics for 3 x 3 cross-channel maps: per band side and
+ * block, over the pixels that are not moving and not saturated in any
+ * channel (0 < v_c < 255 for all c): joint[s][j][10] =
+ * {n, sum R, sum G, sum B, RR, RG, RB, GG, GB, BB}. */
+void orc_strip_joint(const uint8_t *rgb, int64_t rgb_pitch,
+                     const uint8_t *luma, int64_t luma_pitch,
+                     const uint8_t *prev_luma, int64_t prev_pitch,
+                     int W, int H, int S, int B, int T, uint64_t *joint)
+{
+    memset(joint, 0, sizeof(uint64_t) * 2 * B * 10);
+    for (int s = 0; s < 2; ++s) {
+        int x0 = s == 0 ? 0 : W - S;
+        for (int j = 0; j < B; ++j)
+            for (int y = block_row0(j, H, B); y < block_row0(j + 1, H, B); ++y)
+                for (int x = x0; x < x0 + S; ++x) {
+                    if (prev_luma) {
+                        int d = (int)luma[(int64_t)y * luma_pitch + x] -
+                                (int)prev_luma[(int64_t)y * prev_pitch + x];
+                        if (d < 0) d = -d;
+                        if (d > T) continue;
+                    }
+                    const uint8_t *p = rgb + (int64_t)y * rgb_pitch + 3 * x;
+                    int ok = 1;
+                    for (int c = 0; c < 3; ++c)
+                        if (p[c] == 0 || p[c] == 255) ok = 0;
+                    if (!ok) continue;
+                    uint64_t *q = joint + ((int64_t)s * B + j) * 10;
+                    uint64_t r = p[0], g = p[1], b = p[2];
+                    q[0] += 1;
+                    q[1] += r; q[2] += g; q[3] += b;
+                    q[4] += r * r; q[5] += r * g; q[6] += r * b;
+                    q[7] += g * g; q[8] += g * b; q[9] += b * b;
+                }
+    }
+}
+
+/* Apply 3 x 3 cross-channel maps along the ramp: q16 layout [2 sides][B][12]
+ * = {M row-major (9), b (3)} in Q16.  For a pixel of side s, block j and
+ * ramp weight w (orc_ramp_q16):
+ *   A_cd = delta_cd 65536 + floor((m_cd - delta_cd 65536) w / 65536),
+ *   B_c  = floor(b_c w / 65536),
+ *   out_c = clamp(floor((sum_d A_cd v_d + B_c + 32768) / 65536), 0, 255). */
+void orc_apply_matrix(const uint8_t *rgb, int64_t rgb_pitch, int W, int H, int B, const int32_t *q16,
+                      uint8_t *out, int64_t out_pitch)
+{
+    for (int y = 0; y < H; ++y) {
+        int j = 0;
+        while (j + 1 < B && block_row0(j + 1, H, B) <= y) ++j;
+        for (int x = 0; x < W; ++x) {
+            int side = x >= W / 2 ? 1 : 0;
+            int64_t w = orc_ramp_q16(x, W);
+            const int32_t *m = q16 + ((int64_t)side * B + j) * 12;
+            const uint8_t *p = rgb + (int64_t)y * rgb_pitch + 3 * x;
+            for (int c = 0; c < 3; ++c) {
+                int64_t acc = 32768;
+                for (int d = 0; d < 3; ++d) {
+                    int64_t delta = c == d ? 65536 : 0;
+                    int64_t A = delta + floor_div((m[3 * c + d] - delta) * w, 65536);
+                    acc += A * p[d];
+                }
+                acc += floor_div((int64_t)m[9 + c] * w, 65536);
+                int64_t v = floor_div(acc, 65536);
+                out[(int64_t)y * out_pitch + 3 * x + c] = (uint8_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
+            }
+        }
+    }
+}

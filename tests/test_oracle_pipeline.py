@@ -49,7 +49,7 @@ def test_correction_lowers_seam_cost(orc):
     wl = synth.tower12(frames=3)
     wl.cams = [synth.Camera(1024, 540, position=i) for i in range(4)]
     wl.glare_cams = ()
-    for mode, B in ((orc.FIT_GLOBAL, 1), (orc.FIT_SEAM_AFFINE, 16)):
+    for mode, B in ((orc.FIT_GLOBAL, 1), (orc.FIT_SEAM_AFFINE, 16), (orc.FIT_MATRIX, 16)):
         r = _run(orc, wl, orc.Params(fit_mode=mode, num_blocks=B), 2)
         unc = np.mean([seamcost.seam_cost(r["rgb"][k], r["rgb"][k + 1]) for k in range(3)])
         cor = np.mean([seamcost.seam_cost(r["corrected"][k], r["corrected"][k + 1]) for k in range(3)])
