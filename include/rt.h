@@ -57,7 +57,7 @@ typedef enum {
 
 enum { RT_NV12 = 0, RT_MONO16 = 1 };                 /* camera pixel formats         */
 enum { RT_LINEAR = 0, RT_RING = 1 };                 /* seam topology of every chain */
-enum { RT_FIT_GLOBAL = 0, RT_FIT_SEAM_AFFINE = 1, RT_FIT_QUANTILE_AFFINE = 2 };  /* S3 fit */
+enum { RT_FIT_GLOBAL = 0, RT_FIT_SEAM_AFFINE = 1, RT_FIT_QUANTILE_AFFINE = 2, RT_FIT_MATRIX = 3 };  /* S3 fit */
 enum { RT_SCHED_CURRENT = 0, RT_SCHED_LAGGED = 1 };  /* which statistics S5 applies  */
 enum { RT_BT709 = 0, RT_BT601 = 1 };                 /* S1 colour matrix             */
 
@@ -95,7 +95,15 @@ typedef struct {
  *                      line through (band quantile, shared-spectrum quantile)
  *                      pairs at the levels (i + 1/2) / 32; the shared spectrum
  *                      is the equal-weight mixture of the two bands; applied
- *                      like RT_FIT_SEAM_AFFINE);
+ *                      like RT_FIT_SEAM_AFFINE) or RT_FIT_MATRIX (3 x 3
+ *                      cross-channel maps, the conclusion's proposal of linear
+ *                      maps mixing the three channels: per seam side and block
+ *                      the symmetric positive definite M with M S M^T = S_s,
+ *                      S the band's RGB covariance, S_s that of the equal-weight
+ *                      mixture of the two bands, both plus 0.25 I; M's
+ *                      eigenvalues clamped to [gain_min, gain_max];
+ *                      b = mu_s - M mu; moments over pixels neither moving nor
+ *                      saturated in any channel; applied along the ramp);
  *   schedule           RT_SCHED_CURRENT: a frame set is corrected with the
  *                      estimate that includes its own statistics;
  *                      RT_SCHED_LAGGED: with the estimate of the previous
@@ -193,7 +201,10 @@ rt_status rt_submit_frames_host(rt_handle *h, const void *const *y_planes, const
  * side 0 = left half, 1 = right half of the camera; with per-camera gains
  * both sides hold (g, 0).  maps_q16 (may be NULL): the same shape in int32,
  * round(65536 a), round(65536 b) -- the table the pixels were corrected
- * with.  cap = elements each buffer holds (>= K*2*B*3*2). */
+ * with.  With RT_FIT_MATRIX each (camera, side, block) holds 12 values
+ * instead: M row-major (9) then b (3), out_c = sum_d M_cd v_d + b_c.
+ * cap = elements each buffer holds (>= K*2*B*6, or K*2*B*12 for
+ * RT_FIT_MATRIX). */
 rt_status rt_get_gains(rt_handle *h, double *maps_fp64, int32_t *maps_q16, size_t cap, int32_t timeout_ms);
 
 /* Wait for the last submitted frame set and return the device address of
@@ -218,12 +229,16 @@ rt_status rt_get_crops(rt_handle *h, const void **dev_fp16_nchw, int32_t *n, int
  *   strip_sumsq  u64 [K][2][B][3]       sums of squares
  *   frame_hist   u32 [K][3][256]        whole-frame histograms (NULL if off)
  *   thumbs       u32 [K][3][36][64]     thumbnail cell sums (NULL if off)
+ *   strip_joint  u64 [K][2][B][10]      RT_FIT_MATRIX only (else NULL): over
+ *                the band pixels neither moving nor saturated in any channel,
+ *                {n, sum R, sum G, sum B, RR, RG, RB, GG, GB, BB}
  *   uncorrected  optional: NULL (the library keeps no uncorrected RGB). */
 typedef struct {
     const uint32_t *strip_hist, *strip_n;
     const uint64_t *strip_sum, *strip_sumsq;
     const uint32_t *frame_hist, *thumbs;
     int32_t num_cameras, num_blocks;
+    const uint64_t *strip_joint;
 } rt_stats_view;
 rt_status rt_get_stats(rt_handle *h, rt_stats_view *out, int32_t timeout_ms);
 

@@ -6,6 +6,9 @@
 // sequence has no previous frame and removes nothing), and (ii) saturated
 // values 0 and 255 left out per channel.  Counts, sums and sums of squares
 // are the histogram's moments, reduced from it at the end of every CTA.
+// For the 3 x 3 cross-channel maps the kernel also sums the joint moments
+// {n, R, G, B, RR, RG, RB, GG, GB, BB} over the pixels that are not moving
+// and have no saturated channel (registers, then a warp reduction).
 //
 // One CTA per work item (camera, side, rows inside one block); a thread
 // converts 16 band pixels of one row per iteration with one 16-byte load of
@@ -54,6 +57,7 @@ __device__ __forceinline__ uint32_t slot_of(uint32_t vb, int c, bool ok)
     return (ok && v - 1u < 254u) ? (uint32_t)c * 256u + v : 768u;
 }
 
+template <bool JOINT>
 __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const PassAArgs a, int Hmax)
 {
     __shared__ uint32_t sh[3 * 256 + 1];   // + the spare slot
@@ -72,6 +76,9 @@ __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const Pa
     const int xb = it.side == 0 ? 0 : cg.W - a.S;
     const int nrows = it.row1 - it.row0;
     const size_t lbase = (size_t)it.cam * a.luma_cam_stride + (size_t)it.side * Hmax * a.S;
+    // joint moments: n and sums in u32, products in u64 (per unit in u32)
+    uint32_t jn = 0, js[3] = {0u, 0u, 0u};
+    unsigned long long jp[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
     for (int u = threadIdx.x; u < nrows * upr; u += blockDim.x) {
         const int y = it.row0 + u / upr;
         const int x0 = xb + (u % upr) * kUnitCols;
@@ -120,12 +127,27 @@ __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const Pa
             prev[0] = P.x; prev[1] = P.y; prev[2] = P.z; prev[3] = P.w;
         }
         const float T = (float)a.T;
+        uint32_t up[6] = {0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const float d = byte_f(luma[i >> 2], i & 3) - byte_f(prev[i >> 2], i & 3);   // exact
             const bool ok = fabsf(d) <= T;
 #pragma unroll
             for (int c = 0; c < 3; ++c) atomicAdd(&sh[slot_of(vb[i][c], c, ok)], 1u);
+            if constexpr (JOINT) {
+                const uint32_t r = vb[i][0] - kMagicBits, gr = vb[i][1] - kMagicBits, b = vb[i][2] - kMagicBits;
+                const bool jv = ok && r - 1u < 254u && gr - 1u < 254u && b - 1u < 254u;
+                const uint32_t m = jv ? 0xFFFFFFFFu : 0u;
+                const uint32_t rm = r & m, gm = gr & m, bm = b & m;
+                jn += jv ? 1u : 0u;
+                js[0] += rm; js[1] += gm; js[2] += bm;
+                up[0] += rm * rm; up[1] += rm * gm; up[2] += rm * bm;
+                up[3] += gm * gm; up[4] += gm * bm; up[5] += bm * bm;
+            }
+        }
+        if constexpr (JOINT) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) jp[q] += up[q];
         }
     }
     __syncthreads();
@@ -134,8 +156,20 @@ __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const Pa
         const uint32_t cnt = sh[b];
         if (cnt) atomicAdd(a.hist + slot * 256 + b, cnt);
     }
-    // moments of the three channel histograms, one warp per channel in turn
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (JOINT) {
+        unsigned long long v[10] = {jn, js[0], js[1], js[2], jp[0], jp[1], jp[2], jp[3], jp[4], jp[5]};
+#pragma unroll
+        for (int q = 0; q < 10; ++q)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        if (lane == 0 && v[0]) {
+            unsigned long long *dst = a.joint + ((size_t)(it.cam * 2 + it.side) * g.B + it.block) * 10;
+#pragma unroll
+            for (int q = 0; q < 10; ++q) atomicAdd(dst + q, v[q]);
+        }
+    }
+    // moments of the three channel histograms, one warp per channel in turn
     for (int c = warp; c < 3; c += (int)(blockDim.x >> 5)) {
         unsigned long long n = 0, s = 0, ss = 0;
         for (int b = lane; b < 256; b += 32) {
@@ -164,7 +198,8 @@ cudaError_t launch_pass_a(const ArrayGeom &g, const PassAArgs &a, int threads, c
 {
     if (a.n_items == 0) return cudaSuccess;
     const int Hmax = a.luma_cam_stride / (2 * a.S);
-    pass_a_kernel<<<a.n_items, threads, 0, s>>>(g, a, Hmax);
+    if (a.joint) pass_a_kernel<true><<<a.n_items, threads, 0, s>>>(g, a, Hmax);
+    else pass_a_kernel<false><<<a.n_items, threads, 0, s>>>(g, a, Hmax);
     return cudaGetLastError();
 }
 

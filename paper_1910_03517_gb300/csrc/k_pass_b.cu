@@ -98,6 +98,43 @@ __device__ __forceinline__ uint32_t apply_seam(const CamGeom &cg, const int32_t 
     return (uint32_t)t;
 }
 
+// The 12 Q16 values of a 3 x 3 map (M row-major, then b) of one camera,
+// side and row block: three 16-byte loads (each map starts on 48 bytes).
+__device__ __forceinline__ void load_map12(const int32_t *__restrict__ q16, int cam, int side, int j, int B, int (&m)[12])
+{
+    const int4 *p = reinterpret_cast<const int4 *>(q16 + ((size_t)(cam * 2 + side) * B + j) * 12);
+    const int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w;
+    m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
+    m[8] = c.x; m[9] = c.y; m[10] = c.z; m[11] = c.w;
+}
+
+// 3 x 3 map application of one pixel (value bits vb of R, G, B) with ramp
+// weight w:
+//   A_cd = delta_cd 65536 + floor((m_cd - delta_cd 65536) w / 65536),
+//   B_c = floor(b_c w / 65536),
+//   out_c = clamp(floor((sum_d A_cd v_d + B_c + 32768) / 65536), 0, 255),
+// returned with the output byte in byte 2 (t clamped to [0, 0xFFFFFF]).
+// |A_cd| <= 16 * 65536 (eigenvalues of M within the gain limits) keeps the
+// sum inside int32.
+__device__ __forceinline__ void apply_matrix_px(const int (&m)[12], int w, uint32_t vb0, uint32_t vb1, uint32_t vb2,
+                                                uint32_t *t)
+{
+    const int v[3] = {(int)(vb0 - kMagicBits), (int)(vb1 - kMagicBits), (int)(vb2 - kMagicBits)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        int acc = 32768 + (int)(((long long)m[9 + c] * w) >> 16);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int delta = c == d ? 65536 : 0;
+            const int A = delta + (int)(((long long)(m[3 * c + d] - delta) * w) >> 16);
+            acc += A * v[d];
+        }
+        acc = acc < 0 ? 0 : (acc > 0xFFFFFF ? 0xFFFFFF : acc);
+        t[c] = (uint32_t)acc;
+    }
+}
+
 // Thumbnail cell sums of one row's 16 converted pixels (vbits vb[i][c]):
 // cell (i, j) covers columns [floor(i W/64), floor((i+1) W/64)) and rows
 // [floor(j H/36), floor((j+1) H/36)); a unit inside one cell adds three
@@ -190,6 +227,26 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
                 magic2(z1[0], z1[1], vbq[2 * h + 1][0], vbq[2 * h + 1][1]);
                 magic2(z0[2], z1[2], vbq[2 * h][2], vbq[2 * h + 1][2]);
             }
+            if constexpr (FIT == RT_FIT_MATRIX) {
+                // one map load per group of 4 columns, a second one where the
+                // group crosses the image centre (side 0 -> side 1)
+                const int half = cg.W >> 1, xg = x0 + 4 * g4;
+                int m[12];
+                load_map12(q16, cam, xg >= half ? 1 : 0, jr[r], B, m);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = 4 * g4 + q;
+                    const bool live = FULL || i < nvalid;
+                    if (xg < half && xg + q == half) load_map12(q16, cam, 1, jr[r], B, m);
+                    const int w = __ldg(cg.ramp + x0 + (live ? i : 0));
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vbq[q][c];
+                        if (STATS && live) red_shared_inc(hbase + vbq[q][c] * 128u + (uint32_t)c * 32768u);
+                    }
+                    apply_matrix_px(m, w, vbq[q][0], vbq[q][1], vbq[q][2], t + 3 * q);
+                }
+            } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int i = 4 * g4 + q;
@@ -208,6 +265,7 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
                     }
                     t[3 * q + c] = tt;
                 }
+            }
             }
             ow[r][3 * g4 + 0] = pack4(t[0], t[1], t[2], t[3]);
             ow[r][3 * g4 + 1] = pack4(t[4], t[5], t[6], t[7]);
@@ -255,24 +313,42 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
         const int j = block_of_row(y0 + r, cg.H, cg.nblk);
         RowGain rg;
         if (FIT == RT_FIT_GLOBAL) rg = row_gain(q16, cam, j, B);
+        int mm[FIT == RT_FIT_MATRIX ? 12 : 1];
+        int mside = -1;
         uint32_t tv[THUMBS ? kUnitCols : 1][3];
 #pragma unroll
         for (int i = 0; i < kUnitCols; ++i) {
             if (!FULL && i >= nvalid) continue;
             const uint32_t vb = mono_bits((w[i >> 1] >> (16 * (i & 1))) & 0xFFFFu, cg.shift);
             if (THUMBS) tv[THUMBS ? i : 0][0] = tv[THUMBS ? i : 0][1] = tv[THUMBS ? i : 0][2] = vb;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (STATS) red_shared_inc(hbase + vb * 128u + (uint32_t)c * 32768u);
-                uint32_t t;
-                if (FIT == RT_FIT_GLOBAL) {
-                    t = rg.aq[c] * vb + rg.cq[c];
-                    t = t > 0xFFFFFFu ? 0xFFFFFFu : t;
-                } else {
-                    t = apply_seam(cg, q16, cam, j, B, x0 + i, c, vb);
+            if constexpr (FIT == RT_FIT_MATRIX) {
+                const int side = x0 + i >= (cg.W >> 1) ? 1 : 0;
+                if (side != mside) {
+                    load_map12(q16, cam, side, j, B, mm);
+                    mside = side;
                 }
-                const int bb = 3 * i + c;
-                ow[r][bb >> 2] = put_byte2(ow[r][bb >> 2], t, bb & 3);
+                uint32_t t3[3];
+                apply_matrix_px(mm, __ldg(cg.ramp + x0 + i), vb, vb, vb, t3);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (STATS) red_shared_inc(hbase + vb * 128u + (uint32_t)c * 32768u);
+                    const int bb = 3 * i + c;
+                    ow[r][bb >> 2] = put_byte2(ow[r][bb >> 2], t3[c], bb & 3);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (STATS) red_shared_inc(hbase + vb * 128u + (uint32_t)c * 32768u);
+                    uint32_t t;
+                    if (FIT == RT_FIT_GLOBAL) {
+                        t = rg.aq[c] * vb + rg.cq[c];
+                        t = t > 0xFFFFFFu ? 0xFFFFFFu : t;
+                    } else {
+                        t = apply_seam(cg, q16, cam, j, B, x0 + i, c, vb);
+                    }
+                    const int bb = 3 * i + c;
+                    ow[r][bb >> 2] = put_byte2(ow[r][bb >> 2], t, bb & 3);
+                }
             }
         }
         if constexpr (THUMBS) thumb_row<FULL>(th, cg, y0 + r, x0, nvalid, tv);
@@ -295,8 +371,15 @@ constexpr int kHistWords = 3 * 256 * kHistLanes;
 
 constexpr int kThumbWords = RT_THUMB_H * RT_THUMB_W * 3;
 
+// The thumbnail variants and the 3 x 3 maps (twelve map values and three
+// dot products a pixel) get the registers of one CTA per SM.
+template <int FIT, bool THUMBS>
+constexpr bool kOneCtaPerSm = THUMBS || FIT == RT_FIT_MATRIX;
+
 template <int FIT, bool STATS, bool THUMBS>
-__global__ void __launch_bounds__(THUMBS ? 512 : RT_PASS_B_THREADS, THUMBS ? 1 : RT_PASS_B_CTAS_PER_SM) pass_b_kernel(const ArrayGeom g, const PassBArgs a)
+__global__ void __launch_bounds__(kOneCtaPerSm<FIT, THUMBS> ? 512 : RT_PASS_B_THREADS,
+                                  kOneCtaPerSm<FIT, THUMBS> ? 1 : RT_PASS_B_CTAS_PER_SM)
+pass_b_kernel(const ArrayGeom g, const PassBArgs a)
 {
     extern __shared__ uint32_t sh[];
     uint32_t *th = sh + (STATS ? kHistWords : 0);   // [36][64][3] cell sums (THUMBS)
@@ -406,8 +489,8 @@ template <int FIT, bool STATS, bool THUMBS>
 cudaError_t launch_one(const ArrayGeom &g, const PassBArgs &a, int grid, int threads, cudaStream_t s)
 {
     const size_t smem = (size_t)((STATS ? kHistWords : 0) + (THUMBS ? kThumbWords : 0)) * 4;
-    // the thumbnail variant is compiled for at most 512 threads per CTA
-    if (THUMBS && threads > 512) threads = 512;
+    // the one-CTA-per-SM variants are compiled for at most 512 threads per CTA
+    if (kOneCtaPerSm<FIT, THUMBS> && threads > 512) threads = 512;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(threads);
@@ -468,6 +551,7 @@ cudaError_t pass_b_prepare(int threads, size_t *smem_bytes)
     cudaError_t e;
     if ((e = prepare_fit<RT_FIT_GLOBAL>()) != cudaSuccess) return e;
     if ((e = prepare_fit<RT_FIT_SEAM_AFFINE>()) != cudaSuccess) return e;
+    if ((e = prepare_fit<RT_FIT_MATRIX>()) != cudaSuccess) return e;
     *smem_bytes = (size_t)kHistWords * 4;
     return cudaSuccess;
 }
@@ -482,6 +566,12 @@ cudaError_t launch_pass_b(const ArrayGeom &g, const PassBArgs &a, int grid, int 
                                  : launch_one<RT_FIT_GLOBAL, false, true>(g, a, grid, threads, s);
         return stats ? launch_one<RT_FIT_GLOBAL, true, false>(g, a, grid, threads, s)
                      : launch_one<RT_FIT_GLOBAL, false, false>(g, a, grid, threads, s);
+    }
+    if (g.fit_mode == RT_FIT_MATRIX) {
+        if (thumbs) return stats ? launch_one<RT_FIT_MATRIX, true, true>(g, a, grid, threads, s)
+                                 : launch_one<RT_FIT_MATRIX, false, true>(g, a, grid, threads, s);
+        return stats ? launch_one<RT_FIT_MATRIX, true, false>(g, a, grid, threads, s)
+                     : launch_one<RT_FIT_MATRIX, false, false>(g, a, grid, threads, s);
     }
     if (thumbs) return stats ? launch_one<RT_FIT_SEAM_AFFINE, true, true>(g, a, grid, threads, s)
                              : launch_one<RT_FIT_SEAM_AFFINE, false, true>(g, a, grid, threads, s);

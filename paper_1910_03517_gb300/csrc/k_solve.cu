@@ -384,10 +384,11 @@ __global__ void __launch_bounds__(kQuantThreads) solve_quantile_kernel(const Sol
 // C_j = floor(j H / B) + floor((j + 1) H / B) - 1 keep it in integers), the
 // edge blocks' maps beyond the first and last centre:
 //   w = floor(65536 (2y - C_{j-1}) / (C_j - C_{j-1})),
-//   m(y) = m_{j-1} + floor((m_j - m_{j-1}) w / 65536).
-// One thread per (camera, side, row) writes the row's 3 x (a_q, b_q).
+//   m(y) = m_{j-1} + floor((m_j - m_{j-1}) w / 65536),
+// for each of the nv values of a map (6: 3 x (a_q, b_q); 12: a 3 x 3
+// matrix and its offsets).  One thread per (camera, side, row).
 __global__ void __launch_bounds__(256) blend_rows_kernel(const ArrayGeom g, const int32_t *__restrict__ q16, int B,
-                                                         int Hmax, int32_t *__restrict__ rows)
+                                                         int Hmax, int nv, int32_t *__restrict__ rows)
 {
     const int total = g.K * 2 * Hmax;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
@@ -398,19 +399,19 @@ __global__ void __launch_bounds__(256) blend_rows_kernel(const ArrayGeom g, cons
         auto centre = [&](int j) {
             return (int)(((long long)j * H) / B + ((long long)(j + 1) * H) / B - 1);
         };
-        const int32_t *src = q16 + (size_t)(cam * 2 + side) * B * 6;
-        int32_t *dst = rows + ((size_t)(cam * 2 + side) * Hmax + y) * 6;
+        const int32_t *src = q16 + (size_t)(cam * 2 + side) * B * nv;
+        int32_t *dst = rows + ((size_t)(cam * 2 + side) * Hmax + y) * nv;
         if (Y <= centre(0)) {
-            for (int i = 0; i < 6; ++i) dst[i] = src[i];
+            for (int i = 0; i < nv; ++i) dst[i] = src[i];
         } else if (Y >= centre(B - 1)) {
-            for (int i = 0; i < 6; ++i) dst[i] = src[(B - 1) * 6 + i];
+            for (int i = 0; i < nv; ++i) dst[i] = src[(B - 1) * nv + i];
         } else {
             int j = 1;
             while (Y >= centre(j)) ++j;
             const int c0 = centre(j - 1), c1 = centre(j);
             const long long w = (65536LL * (Y - c0)) / (c1 - c0);
-            for (int i = 0; i < 6; ++i) {
-                const long long m0 = src[(j - 1) * 6 + i], m1 = src[j * 6 + i];
+            for (int i = 0; i < nv; ++i) {
+                const long long m0 = src[(j - 1) * nv + i], m1 = src[j * nv + i];
                 dst[i] = (int32_t)(m0 + (((m1 - m0) * w) >> 16));
             }
         }
@@ -419,10 +420,11 @@ __global__ void __launch_bounds__(256) blend_rows_kernel(const ArrayGeom g, cons
 
 }  // namespace
 
-cudaError_t launch_blend_rows(const ArrayGeom &g, const int32_t *q16, int B, int Hmax, int32_t *rows, cudaStream_t s)
+cudaError_t launch_blend_rows(const ArrayGeom &g, const int32_t *q16, int B, int Hmax, int nv, int32_t *rows,
+                              cudaStream_t s)
 {
     const int total = g.K * 2 * Hmax;
-    blend_rows_kernel<<<(total + 255) / 256, 256, 0, s>>>(g, q16, B, Hmax, rows);
+    blend_rows_kernel<<<(total + 255) / 256, 256, 0, s>>>(g, q16, B, Hmax, nv, rows);
     return cudaGetLastError();
 }
 
@@ -459,6 +461,8 @@ cudaError_t launch_solve(const SolveArgs &args, cudaStream_t s)
         a.xhi_f = (float)a.xhi;
         const int n_sys = a.n_groups * a.B * 3;
         solve_global_kernel<<<n_sys, 32, 0, s>>>(a);
+    } else if (args.fit_mode == RT_FIT_MATRIX) {
+        return launch_solve_matrix(args, s);
     } else if (args.fit_mode == RT_FIT_QUANTILE_AFFINE) {
         const int n_ent = args.K * 2 * args.B * 3;
         solve_quantile_kernel<<<(n_ent + kQuantThreads - 1) / kQuantThreads, kQuantThreads, 0, s>>>(args);

@@ -69,6 +69,7 @@ struct rt_handle {
     uint32_t *strip_hist[3] = {nullptr, nullptr, nullptr};
     uint32_t *strip_n[3] = {nullptr, nullptr, nullptr};
     unsigned long long *strip_sum[3] = {nullptr, nullptr, nullptr}, *strip_sumsq[3] = {nullptr, nullptr, nullptr};
+    unsigned long long *strip_joint[3] = {nullptr, nullptr, nullptr};   // [K][2][B][10] (3 x 3 maps)
     uint8_t *luma[2] = {nullptr, nullptr};
     size_t luma_cam_stride = 0;
     double *maps_new = nullptr, *E = nullptr;
@@ -137,7 +138,7 @@ struct rt_handle {
     rt_tuning tuned{};
     size_t pb_smem = 0;
     std::string err;
-    size_t n_maps = 0;             // K*2*B*3*2
+    size_t n_maps = 0;             // K*2*B*6, or K*2*B*12 for the 3 x 3 maps
     // surrogate inference buffers (allocated on first use)
     void *sg_x = nullptr;          // BF16 [K][6912]
     float *sg_y = nullptr;         // [K][3]
@@ -228,7 +229,8 @@ rt_status validate(const rt_array_params *p)
         return fail(nullptr, RT_ERR_INVALID, "strip_width must be a positive multiple of 16");
     if (p->num_blocks < 1 || p->num_blocks > RT_MAX_BLOCKS)
         return fail(nullptr, RT_ERR_INVALID, "num_blocks must be in 1..64");
-    if (p->fit_mode != RT_FIT_GLOBAL && p->fit_mode != RT_FIT_SEAM_AFFINE && p->fit_mode != RT_FIT_QUANTILE_AFFINE)
+    if (p->fit_mode != RT_FIT_GLOBAL && p->fit_mode != RT_FIT_SEAM_AFFINE && p->fit_mode != RT_FIT_QUANTILE_AFFINE &&
+        p->fit_mode != RT_FIT_MATRIX)
         return fail(nullptr, RT_ERR_INVALID, "bad fit_mode");
     if (p->schedule != RT_SCHED_CURRENT && p->schedule != RT_SCHED_LAGGED)
         return fail(nullptr, RT_ERR_INVALID, "bad schedule");
@@ -404,8 +406,11 @@ rt_status setup(rt_handle *h)
         const size_t nb = (size_t)K * 2 * B;
         if ((s = dalloc(h, &h->strip_hist[i], nb * 768 + nb * 3)) != RT_OK) return s;
         h->strip_n[i] = h->strip_hist[i] + nb * 768;
-        if ((s = dalloc(h, &h->strip_sum[i], nb * 3 * 2)) != RT_OK) return s;
+        // joint moments of the 3 x 3 fit follow the sums in the same range
+        const size_t joint = p.fit_mode == RT_FIT_MATRIX ? nb * 10 : 0;
+        if ((s = dalloc(h, &h->strip_sum[i], nb * 3 * 2 + joint)) != RT_OK) return s;
         h->strip_sumsq[i] = h->strip_sum[i] + nb * 3;
+        h->strip_joint[i] = joint ? h->strip_sum[i] + nb * 6 : nullptr;
     }
     for (int i = 0; i < 2; ++i) {
         rt_status s;
@@ -423,7 +428,7 @@ rt_status setup(rt_handle *h)
         }
     }
     if (p.max_crops > 0) RT_CUDA(h, cudaMallocHost((void **)&h->crop_host, sizeof(rt_crop) * 2 * p.max_crops));
-    h->n_maps = (size_t)K * 2 * B * 3 * 2;
+    h->n_maps = (size_t)K * 2 * B * map_vals(p.fit_mode);
     rt_status s;
     if ((s = dalloc(h, &h->maps_new, h->n_maps)) != RT_OK) return s;
     if ((s = dalloc(h, &h->E, h->n_maps)) != RT_OK) return s;
@@ -432,7 +437,11 @@ rt_status setup(rt_handle *h)
     if ((s = dalloc(h, &h->q16_identity, h->n_maps)) != RT_OK) return s;
     {
         std::vector<int32_t> id(h->n_maps);
-        for (size_t i = 0; i < h->n_maps; ++i) id[i] = (i % 2 == 0) ? 65536 : 0;
+        const int nv = map_vals(p.fit_mode);
+        for (size_t i = 0; i < h->n_maps; ++i) {
+            const int v = (int)(i % nv);
+            id[i] = (nv == 12 ? (v == 0 || v == 4 || v == 8) : v % 2 == 0) ? 65536 : 0;
+        }
         RT_CUDA(h, cudaMemcpy(h->q16_identity, id.data(), id.size() * 4, cudaMemcpyHostToDevice));
     }
     // Q16 ramp weight per column, for the seam maps
@@ -503,7 +512,7 @@ rt_status setup(rt_handle *h)
     // pass B launch shape: a persistent grid of all resident CTAs
     if ((p.flags & RT_FLAG_BLEND_BLOCKS) && B > 1)
         for (int i = 0; i < 2; ++i)
-            if ((s = dalloc(h, &h->q16_rows[i], (size_t)K * 2 * h->Hmax * 6)) != RT_OK) return s;
+            if ((s = dalloc(h, &h->q16_rows[i], (size_t)K * 2 * h->Hmax * map_vals(p.fit_mode))) != RT_OK) return s;
     // difference attention: luma copies, cells, proposals
     if (p.flags & RT_FLAG_ATTENTION) {
         AttnArgs &a = h->attn;
@@ -675,7 +684,8 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     pa.hist = h->strip_hist[ss]; pa.n = h->strip_n[ss]; pa.sum = h->strip_sum[ss]; pa.sumsq = h->strip_sumsq[ss];
     const size_t nb = (size_t)K * 2 * p.num_blocks;
     pa.clear_u32 = h->strip_hist[ss_next]; pa.clear_u32_n = nb * 768 + nb * 3;
-    pa.clear_u64 = h->strip_sum[ss_next]; pa.clear_u64_n = nb * 3 * 2;
+    pa.joint = h->strip_joint[ss];
+    pa.clear_u64 = h->strip_sum[ss_next]; pa.clear_u64_n = nb * 3 * 2 + (pa.joint ? nb * 10 : 0);
     RT_CUDA(h, launch_pass_a(g, pa, h->pa_threads, h->s_stats));
     if (prof_chain) RT_CUDA(h, prof_record(h, pe.a1, h->s_stats));
     RT_CUDA(h, cudaEventRecord(h->ev_a[ev], h->s_stats));
@@ -683,6 +693,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
 
     SolveArgs sa{};
     sa.n = h->strip_n[ss]; sa.sum = h->strip_sum[ss]; sa.sumsq = h->strip_sumsq[ss]; sa.hist = h->strip_hist[ss];
+    sa.joint = h->strip_joint[ss];
     sa.maps_new = h->maps_new; sa.E = h->E; sa.q16 = h->q16[qs];
     sa.K = K; sa.B = p.num_blocks; sa.S = p.strip_width; sa.fit_mode = p.fit_mode; sa.min_valid = p.min_valid;
     sa.first = first ? 1 : 0; sa.alpha = p.alpha; sa.lambda = p.lambda; sa.gmin = p.gain_min; sa.gmax = p.gain_max;
@@ -719,7 +730,8 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     pb.q16 = q_apply; pb.frame_hist = fh; pb.thumbs = th;
     if (h->q16_rows[0]) {
         // one blended map per row: the table pass B reads has Hmax "blocks"
-        RT_CUDA(h, launch_blend_rows(g, q_apply, p.num_blocks, h->Hmax, h->q16_rows[par], h->s_main));
+        RT_CUDA(h, launch_blend_rows(g, q_apply, p.num_blocks, h->Hmax, map_vals(p.fit_mode), h->q16_rows[par],
+                                     h->s_main));
         pb.q16 = h->q16_rows[par];
         g.B = h->Hmax;
     }
@@ -728,8 +740,8 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     if (h->seams && dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_seam[ev2], 0));
     if (prof) RT_CUDA(h, prof_record(h, pe.b0, h->s_main));
     // the thumbnail variant with frame statistics needs the shared memory of
-    // one CTA per SM
-    const int pb_grid = (fh && th) ? h->sm_count : h->pb_grid;
+    // one CTA per SM, the 3 x 3 maps its registers
+    const int pb_grid = ((fh && th) || p.fit_mode == RT_FIT_MATRIX) ? h->sm_count : h->pb_grid;
     RT_CUDA(h, launch_pass_b(g, pb, pb_grid, h->pb_threads, h->pb_smem, h->s_main));
     if (prof) RT_CUDA(h, prof_record(h, pe.b1, h->s_main));
     const bool from_props = n_crops == RT_CROPS_FROM_PROPOSALS;
@@ -1011,6 +1023,7 @@ rt_status rt_get_stats(rt_handle *h, rt_stats_view *out, int32_t timeout_ms)
     out->strip_n = h->strip_n[ss];
     out->strip_sum = reinterpret_cast<const uint64_t *>(h->strip_sum[ss]);
     out->strip_sumsq = reinterpret_cast<const uint64_t *>(h->strip_sumsq[ss]);
+    out->strip_joint = reinterpret_cast<const uint64_t *>(h->strip_joint[ss]);
     out->frame_hist = (h->p.flags & RT_FLAG_FRAME_STATS) ? h->frame_hist[par] : nullptr;
     out->thumbs = (h->p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[par] : nullptr;
     out->num_cameras = h->p.num_cameras;

@@ -33,6 +33,10 @@ namespace rt {
 #endif
 
 constexpr int kUnitCols = 16;          // columns a thread converts per row
+
+// Values of one (camera, side, block) map: 3 channels x (a, b), or a 3 x 3
+// cross-channel matrix (row-major) and its offset vector.
+__host__ __device__ constexpr int map_vals(int fit_mode) { return fit_mode == RT_FIT_MATRIX ? 12 : 6; }
 constexpr int kHistLanes = 32;         // lane-private copies of each histogram bin
 
 struct CamGeom {
@@ -86,6 +90,7 @@ struct PassAArgs {
     uint32_t *hist;             // [K][2][B][3][256]
     uint32_t *n;                // [K][2][B][3]
     unsigned long long *sum, *sumsq;
+    unsigned long long *joint;  // [K][2][B][10] joint moments (3 x 3 maps), or nullptr
     // the other slot's statistics (read by the previous solve), cleared here
     // for the next frame set
     uint32_t *clear_u32; size_t clear_u32_n;
@@ -122,9 +127,12 @@ struct SolveArgs {
     const uint32_t *hist;      // [K][2][B][3][256] band histograms (quantile fit)
     const uint32_t *n;
     const unsigned long long *sum, *sumsq;
-    double *maps_new;          // [K][2][B][3][2] this frame set's estimate
-    double *E;                 // [K][2][B][3][2] smoothed estimate (state)
-    int32_t *q16;              // [K][2][B][3][2]
+    const unsigned long long *joint;   // [K][2][B][10] joint moments (3 x 3 maps)
+    // [K][2][B][3][2] = (a, b) per channel, or [K][2][B][12] = (M row-major, b)
+    // for the 3 x 3 maps
+    double *maps_new;          // this frame set's estimate
+    double *E;                 // smoothed estimate (state)
+    int32_t *q16;
     int32_t K, B, S, fit_mode, min_valid, first;
     double alpha, lambda, gmin, gmax;
     // seam chains
@@ -177,7 +185,9 @@ cudaError_t launch_seam_cost(const ArrayGeom &g, const int2 *seams, int n_seams,
 cudaError_t launch_attention(const ArrayGeom &g, const AttnArgs &a, int sm_count, cudaStream_t s);
 // Per-row maps by convex blending of adjacent blocks: rows[K][2][Hmax][3][2]
 // from q16[K][2][B][3][2].
-cudaError_t launch_blend_rows(const ArrayGeom &g, const int32_t *q16, int B, int Hmax, int32_t *rows, cudaStream_t s);
+cudaError_t launch_solve_matrix(const SolveArgs &a, cudaStream_t s);
+cudaError_t launch_blend_rows(const ArrayGeom &g, const int32_t *q16, int B, int Hmax, int nv, int32_t *rows,
+                              cudaStream_t s);
 cudaError_t launch_thumb_features(const ArrayGeom &g, const uint32_t *thumbs, void *out, cudaStream_t s);
 cudaError_t launch_surrogate_gains(const float *y, const int32_t *group_start, const int32_t *group_members,
                                    int n_groups, const double *maps_fit, double gmin, double gmax, double *maps_out,

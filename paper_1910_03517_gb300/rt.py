@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "librt.so")
 RT_OK, RT_ERR_INVALID, RT_ERR_CUDA, RT_ERR_OOM, RT_ERR_NOT_READY, RT_ERR_TIMEOUT, RT_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 RT_NV12, RT_MONO16 = 0, 1
 RT_LINEAR, RT_RING = 0, 1
-RT_FIT_GLOBAL, RT_FIT_SEAM_AFFINE, RT_FIT_QUANTILE_AFFINE = 0, 1, 2
+RT_FIT_GLOBAL, RT_FIT_SEAM_AFFINE, RT_FIT_QUANTILE_AFFINE, RT_FIT_MATRIX = 0, 1, 2, 3
 RT_SCHED_CURRENT, RT_SCHED_LAGGED = 0, 1
 RT_BT709, RT_BT601 = 0, 1
 RT_FLAG_FRAME_STATS = 1
@@ -75,7 +75,8 @@ class Tuning(ctypes.Structure):
 
 class StatsView(ctypes.Structure):
     _fields_ = [("strip_hist", c_vp), ("strip_n", c_vp), ("strip_sum", c_vp), ("strip_sumsq", c_vp),
-                ("frame_hist", c_vp), ("thumbs", c_vp), ("num_cameras", c_i32), ("num_blocks", c_i32)]
+                ("frame_hist", c_vp), ("thumbs", c_vp), ("num_cameras", c_i32), ("num_blocks", c_i32),
+                ("strip_joint", c_vp)]
 
 
 _lib = None
@@ -326,7 +327,9 @@ class CameraArray:
 
     # -- results ---------------------------------------------------------
     def get_gains(self, timeout_ms: int = 60000):
-        shape = (self.K, 2, self.B, 3, 2)
+        """(maps FP64, maps Q16): [K, 2, B, 3, 2] = (a, b) per channel, or
+        [K, 2, B, 12] = (M row-major, b) for the 3 x 3 maps."""
+        shape = (self.K, 2, self.B, 12) if self.p.fit_mode == RT_FIT_MATRIX else (self.K, 2, self.B, 3, 2)
         maps = np.zeros(shape, np.float64)
         q = np.zeros(shape, np.int32)
         st = self.L.rt_get_gains(self.h, maps.ctypes.data, q.ctypes.data, maps.size, timeout_ms)
@@ -368,7 +371,8 @@ class CameraArray:
                                      ("strip_sum", v.strip_sum, (K, 2, B, 3), np.uint64),
                                      ("strip_sumsq", v.strip_sumsq, (K, 2, B, 3), np.uint64),
                                      ("frame_hist", v.frame_hist, (K, 3, 256), np.uint32),
-                                     ("thumbs", v.thumbs, (K, 3, 36, 64), np.uint32)):
+                                     ("thumbs", v.thumbs, (K, 3, 36, 64), np.uint32),
+                                     ("strip_joint", v.strip_joint, (K, 2, B, 10), np.uint64)):
             if not ptr:
                 out[name] = None
                 continue

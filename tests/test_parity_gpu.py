@@ -47,6 +47,17 @@ def _check_q16(q_gpu, q_orc, E):
         assert not bad.any(), (np.argwhere(bad)[:5], q_gpu[bad][:5], q_orc[bad][:5])
 
 
+def _check_matrix_maps(maps, E, rtol, t):
+    """3 x 3 maps compared norm-wise per map: |dM| <= rtol max|M|, and the
+    offsets |db| <= rtol (|b| + 255 max|M|) (b = mu_s - M mu inherits M's
+    error times a mean of up to 255)."""
+    scale = np.abs(E[..., :9]).max(axis=-1, keepdims=True)
+    dM = np.abs(maps[..., :9] - E[..., :9])
+    db = np.abs(maps[..., 9:] - E[..., 9:])
+    assert (dM <= rtol * scale).all(), (t, (dM / scale).max())
+    assert (db <= rtol * (np.abs(E[..., 9:]) + 255 * scale)).all(), (t, db.max())
+
+
 def run_sequence(rt, orc, wl, frames, crops_per_frame=0, crop_size=0, device_inputs=True,
                  stats=True, check_images=True, thumbs=False, maps_rtol=1e-6, blend=False, **kw):
     """Submit `frames` frame sets to the GPU and the oracle, compare each."""
@@ -83,11 +94,16 @@ def run_sequence(rt, orc, wl, frames, crops_per_frame=0, crop_size=0, device_inp
         assert np.array_equal(st["strip_sum"], r["strip_sum"]), t
         assert np.array_equal(st["strip_sumsq"], r["strip_sumsq"]), t
         assert np.array_equal(st["strip_hist"], r["strip_hist"]), t
+        if r.get("strip_joint") is not None:
+            assert np.array_equal(st["strip_joint"], r["strip_joint"]), t
         if stats:
             assert np.array_equal(st["frame_hist"], r["frame_hist"]), t
         # FP64 maps
         E = r["E"]
-        assert (np.abs(maps - E) <= maps_rtol * np.abs(E) + 1e-3 * maps_rtol).all(), (t, np.abs(maps - E).max())
+        if maps.shape[-1] == 12:
+            _check_matrix_maps(maps, E, maps_rtol, t)
+        else:
+            assert (np.abs(maps - E) <= maps_rtol * np.abs(E) + 1e-3 * maps_rtol).all(), (t, np.abs(maps - E).max())
         _check_q16(q16, r["q16"], r["maps"])
         if check_images:
             for k in range(K):
@@ -172,6 +188,66 @@ def test_quantile_affine_fit(rt, orc):
     wl.cams = [synth.Camera(640, 480, position=i) for i in range(3)]
     wl.moving_object = True
     run_sequence(rt, orc, wl, 4, fit_mode=2, num_blocks=4, topology=1, schedule=1, maps_rtol=1e-12)
+
+
+def _matrix_residual(rt, wl, frames, **kw):
+    """max over maps of |M S M - S_s| / |S_s| for the GPU's unsmoothed maps of
+    the last frame set (alpha = 1), S and S_s from the GPU's own joint
+    moments (bit-exact to the oracle's): the defining equation, checked
+    without the oracle's eigen-decompositions."""
+    from oracle import core as oc
+    arr = rt.CameraArray(wl.cams, fit_mode=3, alpha=1.0, gain_min=1e-3, gain_max=16.0, **kw)
+    for t in range(frames):
+        arr.submit_frames(synth.frame_set(wl, t, device="cuda"), t, [])
+    maps, _ = arr.get_gains()
+    joint = arr.get_stats()["strip_joint"]
+    arr.close()
+    worst, checked = 0.0, 0
+    for (_, kl, kr) in oc.seams(wl.cams, kw.get("topology", 0)):
+        for j in range(joint.shape[2]):
+            muR, SR = oc.joint_moments(joint[kl, 1, j])
+            muL, SL = oc.joint_moments(joint[kr, 0, j])
+            d = muL - muR
+            Ss = 0.5 * (SL + SR) + 0.25 * np.outer(d, d)
+            for (k, side, S) in ((kl, 1, SR), (kr, 0, SL)):
+                M = maps[k, side, j, :9].reshape(3, 3)
+                ev = np.linalg.eigvalsh(M)
+                if ev.min() <= 1.001e-3 or ev.max() >= 16.0 * (1 - 1e-9):
+                    continue   # the eigenvalue clamp acted: M no longer solves the equation
+                worst = max(worst, np.abs(M @ S @ M - Ss).max() / np.abs(Ss).max())
+                checked += 1
+    assert checked > 0
+    return worst
+
+
+def test_matrix_maps(rt, orc):
+    """3 x 3 cross-channel maps: joint band moments bit-exact, the FP64 maps
+    (FP32 seed refined by FP64 Newton steps) within the FP64 bar of the
+    oracle's eigen-decompositions (the oracle's own evaluation loses up to
+    ~1e-8 on ill-conditioned bands), images bit-exact; a ring under the
+    lagged schedule with a moving object, blended block maps; and the
+    defining equation M S M = S_s to 1e-12."""
+    run_sequence(rt, orc, synth.small_pair(), 6, fit_mode=3, num_blocks=16)
+    wl = synth.small_pair()
+    wl.cams = [synth.Camera(640, 480, position=i) for i in range(3)]
+    wl.moving_object = True
+    run_sequence(rt, orc, wl, 4, fit_mode=3, num_blocks=4, topology=1, schedule=1)
+    run_sequence(rt, orc, synth.small_pair(), 3, fit_mode=3, num_blocks=8, blend=True)
+    assert _matrix_residual(rt, wl, 2, num_blocks=4, topology=1) < 1e-12
+
+
+def test_matrix_maps_clamped_and_mono(rt, orc):
+    """Tight gain limits make the eigenvalue clamp act (the divided-difference
+    path); mono cameras give rank-one band covariances (two equal
+    eigenvalues from the ridge); ragged widths."""
+    run_sequence(rt, orc, synth.small_pair(), 4, fit_mode=3, num_blocks=4, gain_min=0.97, gain_max=1.02)
+    cams = [synth.Camera(200, 120, position=0, y_pitch=208, uv_pitch=208),
+            synth.Camera(220, 90, position=1, y_pitch=224, uv_pitch=224),
+            synth.Camera(96, 40, fmt=synth.MONO16, bit_depth=10, group=1, position=0, y_pitch=192),
+            synth.Camera(96, 64, fmt=synth.MONO16, bit_depth=10, group=1, position=1, y_pitch=192)]
+    wl = synth.Workload("matrix ragged", cams, frames=3, seed=43)
+    run_sequence(rt, orc, wl, 3, fit_mode=3, num_blocks=2, strip_width=16, min_valid=8)
+    assert _matrix_residual(rt, wl, 2, num_blocks=2, strip_width=16, min_valid=8) < 1e-12
 
 
 def test_seam_affine_64_blocks_ring_lagged(rt, orc):
