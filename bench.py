@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=48)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tower12", choices=["tower12", "small", "uneven", "stress"])
-    ap.add_argument("--fit", default="global", choices=["global", "affine"])
+    ap.add_argument("--fit", default="global", choices=list(FITS))
     ap.add_argument("--schedule", default="current", choices=["current", "lagged"])
     ap.add_argument("--ring", type=int, default=0, help="distinct input frame sets (multiple of 6)")
     ap.add_argument("--e2e-steps", type=int, default=120)
@@ -80,6 +80,14 @@ def input_bytes(wl):
     return tot
 
 
+# fit variants: (fit_mode, blocks, description); the modes' values are the
+# C ABI's RT_FIT_* constants
+FITS = {"global": (0, 1, "per-camera gains, 1 block"),
+        "affine": (1, 16, "seam affine maps, 16 blocks"),
+        "quantile": (2, 16, "quantile-LS affine maps, 16 blocks"),
+        "matrix": (3, 16, "3x3 cross-channel maps, 16 blocks")}
+
+
 def array_kwargs(args, wl):
     from paper_1910_03517_gb300 import rt
     flags = rt.RT_FLAG_FRAME_STATS
@@ -88,8 +96,8 @@ def array_kwargs(args, wl):
     if getattr(args, "seam_cost", False):
         flags |= rt.RT_FLAG_SEAM_COST
     kw = dict(flags=flags,
-              fit_mode=rt.RT_FIT_GLOBAL if args.fit == "global" else rt.RT_FIT_SEAM_AFFINE,
-              num_blocks=1 if args.fit == "global" else 16,
+              fit_mode=FITS[args.fit][0],
+              num_blocks=FITS[args.fit][1],
               schedule=rt.RT_SCHED_CURRENT if args.schedule == "current" else rt.RT_SCHED_LAGGED)
     if wl.n_crops:
         kw.update(max_crops=wl.n_crops, crop_size=wl.crop_out)
@@ -98,7 +106,7 @@ def array_kwargs(args, wl):
 
 def config_dict(args, wl, ring_desc):
     d = {"workload": wl.name, "cameras": len(wl.cams), "pixels_per_set": wl.pixels,
-         "fit": ("per-camera gains, 1 block" if args.fit == "global" else "seam affine maps, 16 blocks"),
+         "fit": FITS[args.fit][2],
          "schedule": args.schedule, "crops_per_set": wl.n_crops, "l2": ring_desc}
     if getattr(args, "attention", False):
         d["attention"] = "difference attention on (windows 256, stride 128, >= 655 on-pixels)"
@@ -217,7 +225,7 @@ def time_oracle(wl, args, seconds, threads):
     import oracle
     from oracle import core
     oracle.build()
-    p = core.Params(fit_mode=0 if args.fit == "global" else 1, num_blocks=1 if args.fit == "global" else 16,
+    p = core.Params(fit_mode=FITS[args.fit][0], num_blocks=FITS[args.fit][1],
                     schedule=0 if args.schedule == "current" else 1)
     Hmin = min(c.height for c in wl.cams)
     # calibrate on a 64-row cut
@@ -260,7 +268,7 @@ def run_reference(args):
     import oracle
     from oracle import core
     oracle.build()
-    p = core.Params(fit_mode=0 if args.fit == "global" else 1, num_blocks=1 if args.fit == "global" else 16,
+    p = core.Params(fit_mode=FITS[args.fit][0], num_blocks=FITS[args.fit][1],
                     schedule=0 if args.schedule == "current" else 1)
     total = args.steps + args.warmup
     # each step: one frame set of the array cut to R rows, R sized so the run takes ~2 minutes

@@ -80,59 +80,108 @@ __device__ __forceinline__ RowGain row_gain(const int32_t *__restrict__ q16, int
     return r;
 }
 
-// Seam-map application of channel c at column x (row block j):
-//   A = 65536 + floor((a_q - 65536) w / 65536), Bq = floor(b_q w / 65536),
-//   out = clamp(floor((A v + Bq + 32768) / 65536), 0, 255)
-__device__ __forceinline__ uint32_t apply_seam(const CamGeom &cg, const int32_t *__restrict__ q16,
-                                               int cam, int j, int B, int x, int c, uint32_t vb)
+// Seam maps along the ramp (Sec. "White balance and exposure correction":
+// identity at the image centre, the full map at the border).  For column x
+// with ramp weight w (Q16) and a map value m:
+//   A = delta 65536 + floor((m - delta 65536) w / 65536),  Bq = floor(b_q w / 65536),
+//   out = clamp(floor((sum A v + Bq + 32768) / 65536), 0, 255).
+// floor(d w / 65536) is one 32-bit high multiply: mulhi(4 d, 16384 w) =
+// floor(d w 2^16 / 2^32), exact while |4 d| < 2^31 and 16384 w <= 2^30 --
+// |d| < 2^21 for slopes and matrix entries within the gain limits (<= 16)
+// and |b_q| < 2^29 for offsets of 8-bit data; the map loads pre-shift d and b_q.
+// Per column the coefficients fold the value bits' offset kMagicBits and the
+// rounding term into one constant: t = sum_d A_d vbits_d + cst, output in
+// byte 2 of t (t clamped to [0, 0xFFFFFF]).
+
+// Affine map of one camera, side and row block, pre-shifted:
+// m[2c] = 4 (a_q - 65536), m[2c+1] = 4 b_q (three 8-byte loads; a map starts on 24 bytes).
+__device__ __forceinline__ void load_map6(const int32_t *__restrict__ q16, int cam, int side, int j, int B, int (&m)[6])
 {
-    const int side = x >= (cg.W >> 1) ? 1 : 0;
-    const long long w = __ldg(cg.ramp + x);
-    const int32_t *m = q16 + ((size_t)(cam * 2 + side) * B + j) * 6 + 2 * c;
-    const int aq = __ldg(m), bq = __ldg(m + 1);
-    const int A = 65536 + (int)(((long long)(aq - 65536) * w) >> 16);
-    const int Bq = (int)(((long long)bq * w) >> 16);
-    const uint32_t cst = (uint32_t)(Bq + 32768) - (uint32_t)A * kMagicBits;
-    int t = (int)((uint32_t)A * vb + cst);
-    t = t < 0 ? 0 : (t > 0xFFFFFF ? 0xFFFFFF : t);
-    return (uint32_t)t;
+    const int2 *p = reinterpret_cast<const int2 *>(q16 + ((size_t)(cam * 2 + side) * B + j) * 6);
+    const int2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    m[0] = (a.x - 65536) << 2; m[1] = a.y << 2;
+    m[2] = (b.x - 65536) << 2; m[3] = b.y << 2;
+    m[4] = (c.x - 65536) << 2; m[5] = c.y << 2;
 }
 
-// The 12 Q16 values of a 3 x 3 map (M row-major, then b) of one camera,
-// side and row block: three 16-byte loads (each map starts on 48 bytes).
+// 3 x 3 map, pre-shifted: m[3c+d] = 4 (M_cd - delta_cd 65536), m[9+c] = 4 b_c
+// (three 16-byte loads; a map starts on 48 bytes).
 __device__ __forceinline__ void load_map12(const int32_t *__restrict__ q16, int cam, int side, int j, int B, int (&m)[12])
 {
     const int4 *p = reinterpret_cast<const int4 *>(q16 + ((size_t)(cam * 2 + side) * B + j) * 12);
     const int4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
-    m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w;
-    m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
-    m[8] = c.x; m[9] = c.y; m[10] = c.z; m[11] = c.w;
+    const int v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int i = 0; i < 12; ++i) m[i] = (v[i] - ((i == 0 || i == 4 || i == 8) ? 65536 : 0)) << 2;
 }
 
-// 3 x 3 map application of one pixel (value bits vb of R, G, B) with ramp
-// weight w:
-//   A_cd = delta_cd 65536 + floor((m_cd - delta_cd 65536) w / 65536),
-//   B_c = floor(b_c w / 65536),
-//   out_c = clamp(floor((sum_d A_cd v_d + B_c + 32768) / 65536), 0, 255),
-// returned with the output byte in byte 2 (t clamped to [0, 0xFFFFFF]).
-// |A_cd| <= 16 * 65536 (eigenvalues of M within the gain limits) keeps the
-// sum inside int32.
-__device__ __forceinline__ void apply_matrix_px(const int (&m)[12], int w, uint32_t vb0, uint32_t vb1, uint32_t vb2,
-                                                uint32_t *t)
+// Ramp weights of 4 columns from x (a multiple of 4): one 16-byte load (each
+// camera's ramp starts on 16 bytes and the table has 16 bytes of tail).
+__device__ __forceinline__ int4 ramp4(const int32_t *__restrict__ ramp, int x)
 {
-    const int v[3] = {(int)(vb0 - kMagicBits), (int)(vb1 - kMagicBits), (int)(vb2 - kMagicBits)};
+    return __ldg(reinterpret_cast<const int4 *>(ramp + x));
+}
+
+__device__ __forceinline__ void load_map(const int32_t *__restrict__ q16, int cam, int side, int j, int B, int (&m)[6])
+{
+    load_map6(q16, cam, side, j, B, m);
+}
+__device__ __forceinline__ void load_map(const int32_t *__restrict__ q16, int cam, int side, int j, int B, int (&m)[12])
+{
+    load_map12(q16, cam, side, j, B, m);
+}
+
+__device__ __forceinline__ uint32_t clamp24(uint32_t t)
+{
+    const int v = (int)t;
+    return (uint32_t)(v < 0 ? 0 : (v > 0xFFFFFF ? 0xFFFFFF : v));
+}
+
+// Column coefficients of a map: NV = 6 (affine: A_c, cst_c) or 12 (3 x 3:
+// A_cd row-major, cst_c).  w14 = 16384 w.
+template <int NV> struct ColCoef;
+template <> struct ColCoef<6> { uint32_t A[3], cst[3]; };
+template <> struct ColCoef<12> { uint32_t A[9], cst[3]; };
+
+__device__ __forceinline__ void col_coef(const int (&m)[6], int w14, ColCoef<6> &o)
+{
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        int acc = 32768 + (int)(((long long)m[9 + c] * w) >> 16);
+        const int A = 65536 + __mulhi(m[2 * c], w14);
+        const int Bq = __mulhi(m[2 * c + 1], w14);
+        o.A[c] = (uint32_t)A;
+        o.cst[c] = (uint32_t)(Bq + 32768) - (uint32_t)A * kMagicBits;
+    }
+}
+
+__device__ __forceinline__ void col_coef(const int (&m)[12], int w14, ColCoef<12> &o)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        uint32_t sumA = 0;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const int delta = c == d ? 65536 : 0;
-            const int A = delta + (int)(((long long)(m[3 * c + d] - delta) * w) >> 16);
-            acc += A * v[d];
+            const int A = (c == d ? 65536 : 0) + __mulhi(m[3 * c + d], w14);
+            o.A[3 * c + d] = (uint32_t)A;
+            sumA += (uint32_t)A;
         }
-        acc = acc < 0 ? 0 : (acc > 0xFFFFFF ? 0xFFFFFF : acc);
-        t[c] = (uint32_t)acc;
+        const int Bq = __mulhi(m[9 + c], w14);
+        o.cst[c] = (uint32_t)(Bq + 32768) - sumA * kMagicBits;   // modulo 2^32
     }
+}
+
+// Output words (byte 2 = the 8-bit result) of one pixel's three value bits.
+__device__ __forceinline__ void col_apply(const ColCoef<6> &k, const uint32_t (&vb)[3], uint32_t *t)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) t[c] = clamp24(k.A[c] * vb[c] + k.cst[c]);
+}
+
+__device__ __forceinline__ void col_apply(const ColCoef<12> &k, const uint32_t (&vb)[3], uint32_t *t)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        t[c] = clamp24(k.A[3 * c] * vb[0] + k.A[3 * c + 1] * vb[1] + k.A[3 * c + 2] * vb[2] + k.cst[c]);
 }
 
 // Thumbnail cell sums of one row's 16 converted pixels (vbits vb[i][c]):
@@ -209,67 +258,106 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
             cz[h][1] = fmaf(Uf, k.kgu, fmaf(Vf, k.kgv, k.c_g0));
             cz[h][2] = fmaf(Uf, k.kbu, k.c_b0);
         }
+        if constexpr (FIT == RT_FIT_GLOBAL) {
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            uint32_t t[12];
-            // conversion of the 4 pixels: 12 saturated z, rounded two at a time
-            uint32_t vbq[4][3];
+            for (int r = 0; r < 2; ++r) {
+                uint32_t t[12];
+                // conversion of the 4 pixels: 12 saturated z, rounded two at a time
+                uint32_t vbq[4][3];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {             // pixels 2h, 2h+1 share a chroma pair
-                const float Y0f = byte_f(yw[r][g4], 2 * h), Y1f = byte_f(yw[r][g4], 2 * h + 1);
-                float z0[3], z1[3];
+                for (int h = 0; h < 2; ++h) {             // pixels 2h, 2h+1 share a chroma pair
+                    const float Y0f = byte_f(yw[r][g4], 2 * h), Y1f = byte_f(yw[r][g4], 2 * h + 1);
+                    float z0[3], z1[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    z0[c] = __saturatef(fmaf(Y0f, k.ky, cz[h][c]));
-                    z1[c] = __saturatef(fmaf(Y1f, k.ky, cz[h][c]));
+                    for (int c = 0; c < 3; ++c) {
+                        z0[c] = __saturatef(fmaf(Y0f, k.ky, cz[h][c]));
+                        z1[c] = __saturatef(fmaf(Y1f, k.ky, cz[h][c]));
+                    }
+                    magic2(z0[0], z0[1], vbq[2 * h][0], vbq[2 * h][1]);
+                    magic2(z1[0], z1[1], vbq[2 * h + 1][0], vbq[2 * h + 1][1]);
+                    magic2(z0[2], z1[2], vbq[2 * h][2], vbq[2 * h + 1][2]);
                 }
-                magic2(z0[0], z0[1], vbq[2 * h][0], vbq[2 * h][1]);
-                magic2(z1[0], z1[1], vbq[2 * h + 1][0], vbq[2 * h + 1][1]);
-                magic2(z0[2], z1[2], vbq[2 * h][2], vbq[2 * h + 1][2]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = 4 * g4 + q;
+                    const uint32_t *vb = vbq[q];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vb[c];
+                        const bool live = FULL || i < nvalid;
+                        if (STATS && live) red_shared_inc(hbase + vb[c] * 128u + (uint32_t)c * 32768u);
+                        uint32_t tt = rg[r].aq[c] * vb[c] + rg[r].cq[c];
+                        tt = tt > 0xFFFFFFu ? 0xFFFFFFu : tt;
+                        t[3 * q + c] = tt;
+                    }
+                }
+                ow[r][3 * g4 + 0] = pack4(t[0], t[1], t[2], t[3]);
+                ow[r][3 * g4 + 1] = pack4(t[4], t[5], t[6], t[7]);
+                ow[r][3 * g4 + 2] = pack4(t[8], t[9], t[10], t[11]);
             }
-            if constexpr (FIT == RT_FIT_MATRIX) {
-                // one map load per group of 4 columns, a second one where the
-                // group crosses the image centre (side 0 -> side 1)
-                const int half = cg.W >> 1, xg = x0 + 4 * g4;
-                int m[12];
-                load_map12(q16, cam, xg >= half ? 1 : 0, jr[r], B, m);
+        } else {
+            // conversion of the 4 pixels of both rows: 12 saturated z per row,
+            // rounded two at a time
+            uint32_t vbq[2][4][3];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {             // pixels 2h, 2h+1 share a chroma pair
+                    const float Y0f = byte_f(yw[r][g4], 2 * h), Y1f = byte_f(yw[r][g4], 2 * h + 1);
+                    float z0[3], z1[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        z0[c] = __saturatef(fmaf(Y0f, k.ky, cz[h][c]));
+                        z1[c] = __saturatef(fmaf(Y1f, k.ky, cz[h][c]));
+                    }
+                    magic2(z0[0], z0[1], vbq[r][2 * h][0], vbq[r][2 * h][1]);
+                    magic2(z1[0], z1[1], vbq[r][2 * h + 1][0], vbq[r][2 * h + 1][1]);
+                    magic2(z0[2], z1[2], vbq[r][2 * h][2], vbq[r][2 * h + 1][2]);
+                }
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int i = 4 * g4 + q;
                     const bool live = FULL || i < nvalid;
-                    if (xg < half && xg + q == half) load_map12(q16, cam, 1, jr[r], B, m);
-                    const int w = __ldg(cg.ramp + x0 + (live ? i : 0));
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vbq[q][c];
-                        if (STATS && live) red_shared_inc(hbase + vbq[q][c] * 128u + (uint32_t)c * 32768u);
+                        if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vbq[r][q][c];
+                        if (STATS && live) red_shared_inc(hbase + vbq[r][q][c] * 128u + (uint32_t)c * 32768u);
                     }
-                    apply_matrix_px(m, w, vbq[q][0], vbq[q][1], vbq[q][2], t + 3 * q);
                 }
-            } else {
+            uint32_t t[2][12];
+            // seam maps: the coefficients of a column serve both rows unless
+            // the row pair straddles a block boundary; one map load per group
+            // of 4 columns, another where the group crosses the image centre
+            constexpr int NV = FIT == RT_FIT_MATRIX ? 12 : 6;
+            const int half = cg.W >> 1, xg = x0 + 4 * g4;
+            int m[NV];
+            load_map(q16, cam, xg >= half ? 1 : 0, jr[0], B, m);
+            const int4 w4 = ramp4(cg.ramp, xg);
+            const int wq[4] = {w4.x << 14, w4.y << 14, w4.z << 14, w4.w << 14};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int i = 4 * g4 + q;
-                const uint32_t *vb = vbq[q];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vb[c];
-                    const bool live = FULL || i < nvalid;
-                    if (STATS && live) red_shared_inc(hbase + vb[c] * 128u + (uint32_t)c * 32768u);
-                    uint32_t tt;
-                    if (FIT == RT_FIT_GLOBAL) {
-                        tt = rg[r].aq[c] * vb[c] + rg[r].cq[c];
-                        tt = tt > 0xFFFFFFu ? 0xFFFFFFu : tt;
-                    } else {
-                        tt = apply_seam(cg, q16, cam, jr[r], B, x0 + (live ? i : 0), c, vb[c]);
-                    }
-                    t[3 * q + c] = tt;
+                if (xg < half && xg + q == half) load_map(q16, cam, 1, jr[0], B, m);
+                ColCoef<NV> cc;
+                col_coef(m, wq[q], cc);
+                col_apply(cc, vbq[0][q], &t[0][3 * q]);
+                if (jr[1] == jr[0]) {
+                    col_apply(cc, vbq[1][q], &t[1][3 * q]);
+                } else {
+                    int m1[NV];
+                    load_map(q16, cam, xg + q >= half ? 1 : 0, jr[1], B, m1);
+                    ColCoef<NV> c1;
+                    col_coef(m1, wq[q], c1);
+                    col_apply(c1, vbq[1][q], &t[1][3 * q]);
                 }
             }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                ow[r][3 * g4 + 0] = pack4(t[r][0], t[r][1], t[r][2], t[r][3]);
+                ow[r][3 * g4 + 1] = pack4(t[r][4], t[r][5], t[r][6], t[r][7]);
+                ow[r][3 * g4 + 2] = pack4(t[r][8], t[r][9], t[r][10], t[r][11]);
             }
-            ow[r][3 * g4 + 0] = pack4(t[0], t[1], t[2], t[3]);
-            ow[r][3 * g4 + 1] = pack4(t[4], t[5], t[6], t[7]);
-            ow[r][3 * g4 + 2] = pack4(t[8], t[9], t[10], t[11]);
         }
     }
     if constexpr (THUMBS) {
@@ -313,7 +401,8 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
         const int j = block_of_row(y0 + r, cg.H, cg.nblk);
         RowGain rg;
         if (FIT == RT_FIT_GLOBAL) rg = row_gain(q16, cam, j, B);
-        int mm[FIT == RT_FIT_MATRIX ? 12 : 1];
+        constexpr int NV = FIT == RT_FIT_MATRIX ? 12 : 6;
+        int mm[NV];
         int mside = -1;
         uint32_t tv[THUMBS ? kUnitCols : 1][3];
 #pragma unroll
@@ -321,14 +410,17 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
             if (!FULL && i >= nvalid) continue;
             const uint32_t vb = mono_bits((w[i >> 1] >> (16 * (i & 1))) & 0xFFFFu, cg.shift);
             if (THUMBS) tv[THUMBS ? i : 0][0] = tv[THUMBS ? i : 0][1] = tv[THUMBS ? i : 0][2] = vb;
-            if constexpr (FIT == RT_FIT_MATRIX) {
+            if constexpr (FIT != RT_FIT_GLOBAL) {
                 const int side = x0 + i >= (cg.W >> 1) ? 1 : 0;
                 if (side != mside) {
-                    load_map12(q16, cam, side, j, B, mm);
+                    load_map(q16, cam, side, j, B, mm);
                     mside = side;
                 }
+                ColCoef<NV> cc;
+                col_coef(mm, __ldg(cg.ramp + x0 + i) << 14, cc);
+                const uint32_t v3[3] = {vb, vb, vb};
                 uint32_t t3[3];
-                apply_matrix_px(mm, __ldg(cg.ramp + x0 + i), vb, vb, vb, t3);
+                col_apply(cc, v3, t3);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (STATS) red_shared_inc(hbase + vb * 128u + (uint32_t)c * 32768u);
@@ -339,13 +431,8 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (STATS) red_shared_inc(hbase + vb * 128u + (uint32_t)c * 32768u);
-                    uint32_t t;
-                    if (FIT == RT_FIT_GLOBAL) {
-                        t = rg.aq[c] * vb + rg.cq[c];
-                        t = t > 0xFFFFFFu ? 0xFFFFFFu : t;
-                    } else {
-                        t = apply_seam(cg, q16, cam, j, B, x0 + i, c, vb);
-                    }
+                    uint32_t t = rg.aq[c] * vb + rg.cq[c];
+                    t = t > 0xFFFFFFu ? 0xFFFFFFu : t;
                     const int bb = 3 * i + c;
                     ow[r][bb >> 2] = put_byte2(ow[r][bb >> 2], t, bb & 3);
                 }
@@ -371,10 +458,10 @@ constexpr int kHistWords = 3 * 256 * kHistLanes;
 
 constexpr int kThumbWords = RT_THUMB_H * RT_THUMB_W * 3;
 
-// The thumbnail variants and the 3 x 3 maps (twelve map values and three
-// dot products a pixel) get the registers of one CTA per SM.
+// The thumbnail variants and the seam maps (per-column coefficients of both
+// rows of a unit in registers) get the registers of one CTA per SM.
 template <int FIT, bool THUMBS>
-constexpr bool kOneCtaPerSm = THUMBS || FIT == RT_FIT_MATRIX;
+constexpr bool kOneCtaPerSm = THUMBS || FIT != RT_FIT_GLOBAL;
 
 template <int FIT, bool STATS, bool THUMBS>
 __global__ void __launch_bounds__(kOneCtaPerSm<FIT, THUMBS> ? 512 : RT_PASS_B_THREADS,

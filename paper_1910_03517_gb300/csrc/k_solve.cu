@@ -328,55 +328,94 @@ const SolveTables &solve_tables()
     return t;
 }
 
-// Quantile-LS affine maps: one thread per (camera, side, block, channel).
-// One pass over the 256 bins of both bands of the seam assigns this side's
-// 32 quantiles and the mixture's 32 (every comparison on exact integers);
-// the slope is the ratio of two exact integer sums, b follows without FMA
-// contraction -- the oracle's arithmetic, operation for operation.
+// Quantile-LS affine maps: one warp per (camera, side, block, channel).
+// Lane l holds bins 8l .. 8l+7 of both bands' histograms; a warp scan gives
+// the cumulative counts c_R(v), c_L(v) in shared memory.  Lane i then finds,
+// by binary search over v, its band's quantile x_i (the smallest v with
+// 2 Q c_S(v) >= (2i + 1) n_S) and the mixture's y_i (the smallest v with
+// Q (c_R(v) n_L + c_L(v) n_R) >= (2i + 1) n_R n_L), every comparison on exact
+// integers; the line's integer sums come from a warp reduction, the slope is
+// the ratio of two exact integer sums and b follows without FMA contraction
+// -- the oracle's arithmetic, operation for operation.
 constexpr int kQuantiles = 32;
-constexpr int kQuantThreads = 64;
+constexpr int kQuantWarps = 4;
 
-__global__ void __launch_bounds__(kQuantThreads) solve_quantile_kernel(const SolveArgs a)
+__global__ void __launch_bounds__(32 * kQuantWarps) solve_quantile_kernel(const SolveArgs a)
 {
-    __shared__ uint8_t sx[kQuantThreads][kQuantiles], sy[kQuantThreads][kQuantiles];
-    const int n_ent = a.K * 2 * a.B * 3;
-    const int t = threadIdx.x;
-    for (int e = blockIdx.x * blockDim.x + t; e < n_ent; e += gridDim.x * blockDim.x) {
-        const int c = e % 3, j = (e / 3) % a.B, side = (e / (3 * a.B)) % 2, cam = e / (6 * a.B);
-        const int nb = side == 1 ? a.right_nbr[cam] : a.left_nbr[cam];
-        double va = 1.0, vb = 0.0;
-        if (nb >= 0 && nb != cam) {
-            const int kl = side == 1 ? cam : nb, kr = side == 1 ? nb : cam;
-            const size_t iR = ((size_t)(kl * 2 + 1) * a.B + j) * 3 + c;
-            const size_t iL = ((size_t)(kr * 2 + 0) * a.B + j) * 3 + c;
-            const long long nR = a.n[iR], nL = a.n[iL];
-            if (nR >= a.min_valid && nL >= a.min_valid) {
-                const uint32_t *hR = a.hist + iR * 256, *hL = a.hist + iL * 256;
-                const long long nS = side == 1 ? nR : nL;       // this side's band
-                long long cR = 0, cL = 0;
-                int ix = 0, iy = 0;
-                for (int v = 0; v < 256 && (ix < kQuantiles || iy < kQuantiles); ++v) {
-                    cR += hR[v];
-                    cL += hL[v];
-                    const long long cS = side == 1 ? cR : cL;
-                    while (ix < kQuantiles && 2LL * kQuantiles * cS >= (2LL * ix + 1) * nS) sx[t][ix++] = (uint8_t)v;
-                    while (iy < kQuantiles && kQuantiles * (cR * nL + cL * nR) >= (2LL * iy + 1) * nR * nL)
-                        sy[t][iy++] = (uint8_t)v;
-                }
-                long long Sx = 0, Sy = 0, Sxx = 0, Sxy = 0;
-                for (int i = 0; i < kQuantiles; ++i) {
-                    const long long x = sx[t][i], y = sy[t][i];
-                    Sx += x; Sy += y; Sxx += x * x; Sxy += x * y;
-                }
-                const long long den = kQuantiles * Sxx - Sx * Sx, num = kQuantiles * Sxy - Sx * Sy;
-                double s = den != 0 ? (double)num / (double)den : 1.0;
-                s = fmin(fmax(s, a.gmin), a.gmax);
-                va = s;
-                vb = __ddiv_rn(__dsub_rn((double)Sy, __dmul_rn(s, (double)Sx)), (double)kQuantiles);
+    __shared__ uint32_t cum[kQuantWarps][2][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int e = blockIdx.x * kQuantWarps + warp;
+    if (e >= a.K * 2 * a.B * 3) return;   // whole warp
+    const int c = e % 3, j = (e / 3) % a.B, side = (e / (3 * a.B)) % 2, cam = e / (6 * a.B);
+    const int nb = side == 1 ? a.right_nbr[cam] : a.left_nbr[cam];
+    double va = 1.0, vb = 0.0;
+    if (nb >= 0 && nb != cam) {
+        const int kl = side == 1 ? cam : nb, kr = side == 1 ? nb : cam;
+        const size_t iR = ((size_t)(kl * 2 + 1) * a.B + j) * 3 + c;
+        const size_t iL = ((size_t)(kr * 2 + 0) * a.B + j) * 3 + c;
+        const long long nR = a.n[iR], nL = a.n[iL];
+        if (nR >= a.min_valid && nL >= a.min_valid) {   // warp-uniform
+            const uint4 *hR = reinterpret_cast<const uint4 *>(a.hist + iR * 256) + 2 * lane;
+            const uint4 *hL = reinterpret_cast<const uint4 *>(a.hist + iL * 256) + 2 * lane;
+            const uint4 r0 = hR[0], r1 = hR[1], l0 = hL[0], l1 = hL[1];
+            uint32_t cr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            uint32_t cl[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+#pragma unroll
+            for (int q = 1; q < 8; ++q) {
+                cr[q] += cr[q - 1];
+                cl[q] += cl[q - 1];
             }
+            // exclusive prefix of the lanes' totals
+            uint32_t pr = cr[7], pl = cl[7];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t ur = __shfl_up_sync(0xffffffffu, pr, o), ul = __shfl_up_sync(0xffffffffu, pl, o);
+                if (lane >= o) { pr += ur; pl += ul; }
+            }
+            pr -= cr[7];
+            pl -= cl[7];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                cum[warp][0][8 * lane + q] = cr[q] + pr;
+                cum[warp][1][8 * lane + q] = cl[q] + pl;
+            }
+            __syncwarp();
+            const uint32_t *cR = cum[warp][0], *cL = cum[warp][1];
+            const long long nS = side == 1 ? nR : nL;
+            const uint32_t *cS = side == 1 ? cR : cL;
+            const long long lev = 2LL * lane + 1;
+            // smallest v in [0, 255] with the predicate true (true at 255)
+            int lo = 0, hi = 255;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (2LL * kQuantiles * cS[mid] >= lev * nS) hi = mid; else lo = mid + 1;
+            }
+            const int x = lo;
+            lo = 0; hi = 255;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((long long)kQuantiles * ((long long)cR[mid] * nL + (long long)cL[mid] * nR) >= lev * nR * nL)
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            const int y = lo;
+            long long Sx = x, Sy = y, Sxx = x * x, Sxy = x * y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                Sx += __shfl_xor_sync(0xffffffffu, Sx, o);
+                Sy += __shfl_xor_sync(0xffffffffu, Sy, o);
+                Sxx += __shfl_xor_sync(0xffffffffu, Sxx, o);
+                Sxy += __shfl_xor_sync(0xffffffffu, Sxy, o);
+            }
+            const long long den = kQuantiles * Sxx - Sx * Sx, num = kQuantiles * Sxy - Sx * Sy;
+            double s = den != 0 ? (double)num / (double)den : 1.0;
+            s = fmin(fmax(s, a.gmin), a.gmax);
+            va = s;
+            vb = __ddiv_rn(__dsub_rn((double)Sy, __dmul_rn(s, (double)Sx)), (double)kQuantiles);
         }
-        smooth_store(a, (size_t)e * 2, va, vb);
     }
+    if (lane == 0) smooth_store(a, (size_t)e * 2, va, vb);
 }
 
 // Per-row maps by convex combination of adjacent blocks' maps: linear
@@ -465,7 +504,7 @@ cudaError_t launch_solve(const SolveArgs &args, cudaStream_t s)
         return launch_solve_matrix(args, s);
     } else if (args.fit_mode == RT_FIT_QUANTILE_AFFINE) {
         const int n_ent = args.K * 2 * args.B * 3;
-        solve_quantile_kernel<<<(n_ent + kQuantThreads - 1) / kQuantThreads, kQuantThreads, 0, s>>>(args);
+        solve_quantile_kernel<<<(n_ent + kQuantWarps - 1) / kQuantWarps, 32 * kQuantWarps, 0, s>>>(args);
     } else {
         const int n_ent = args.K * 2 * args.B * 3;
         solve_affine_kernel<<<(n_ent + 63) / 64, 64, 0, s>>>(args);

@@ -444,16 +444,20 @@ rt_status setup(rt_handle *h)
         }
         RT_CUDA(h, cudaMemcpy(h->q16_identity, id.data(), id.size() * 4, cudaMemcpyHostToDevice));
     }
-    // Q16 ramp weight per column, for the seam maps
+    // Q16 ramp weight per column, for the seam maps; each camera's ramp
+    // starts on 16 bytes and 16 bytes of tail follow the last one (pass B
+    // reads the weights of 4 columns at a time, past a ragged row end)
     {
         std::vector<int32_t> rmp;
         std::vector<size_t> roff(K);
         for (int k = 0; k < K; ++k) {
+            while (rmp.size() % 4) rmp.push_back(0);
             roff[k] = rmp.size();
             const long long W = h->cams[k].width, half = W / 2;
             for (long long x = 0; x < W; ++x)
                 rmp.push_back((int32_t)(x < half ? ((half - x) * 65536) / half : ((x - half + 1) * 65536) / half));
         }
+        for (int i = 0; i < 4; ++i) rmp.push_back(0);
         if ((s = dalloc(h, &h->ramp, rmp.size())) != RT_OK) return s;
         RT_CUDA(h, cudaMemcpy(h->ramp, rmp.data(), rmp.size() * 4, cudaMemcpyHostToDevice));
         for (int k = 0; k < K; ++k) g.cam[k].ramp = h->ramp + roff[k];
@@ -740,8 +744,8 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     if (h->seams && dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_seam[ev2], 0));
     if (prof) RT_CUDA(h, prof_record(h, pe.b0, h->s_main));
     // the thumbnail variant with frame statistics needs the shared memory of
-    // one CTA per SM, the 3 x 3 maps its registers
-    const int pb_grid = ((fh && th) || p.fit_mode == RT_FIT_MATRIX) ? h->sm_count : h->pb_grid;
+    // one CTA per SM, the seam maps its registers
+    const int pb_grid = ((fh && th) || p.fit_mode != RT_FIT_GLOBAL) ? h->sm_count : h->pb_grid;
     RT_CUDA(h, launch_pass_b(g, pb, pb_grid, h->pb_threads, h->pb_smem, h->s_main));
     if (prof) RT_CUDA(h, prof_record(h, pe.b1, h->s_main));
     const bool from_props = n_crops == RT_CROPS_FROM_PROPOSALS;
