@@ -348,8 +348,10 @@ def surrogate_report(args):
         _, jerr = arr.surrogate_predict(net)
     t_pred = (time.perf_counter() - t0) / reps
     arr.close()
+    seq = quality_sequence(net, n_cams, W, H)
     net.close()
     return {
+        "sequence": seq,
         "train_samples": int(Xtr.shape[0]), "train_epochs": 6, "data_seconds": round(t_data, 1),
         "train_seconds": round(t_train, 2), "train_samples_per_s": round(6 * Xtr.shape[0] / t_train),
         "final_loss": float(np.mean(losses[-10:])),
@@ -362,6 +364,38 @@ def surrogate_report(args):
         "note": ("surrogate = thumbnail features + tcgen05 MLP + re-gauge + judge (host-synchronous call); "
                  "plain chain = band statistics + FP64 solve (device time, overlapped with pass B in the pipeline)"),
     }
+
+
+def quality_sequence(net, n_cams, W, H, frames=30):
+    """A moving object crossing seams, camera gains drifting 1 % a frame:
+    frame-to-frame jitter of the log-gains (mean |ln g_t - ln g_{t-1}| over
+    cameras and channels) and the mean seam cost of the corrected output
+    (Eq. gradientcost) under the CURRENT and LAGGED schedules, and the jitter
+    of the surrogate's raw predictions on the same frames."""
+    import numpy as np
+    from paper_1910_03517_gb300 import rt, surrogate as sg, synth
+    wl = sg.training_workload(n_cams, W, H, seed=123)
+    wl.moving_object, wl.gain_walk, wl.frames = True, 0.01, frames
+    out = {"frames": frames, "cameras": n_cams, "size": "%dx%d" % (W, H)}
+    for name, sched in (("current", rt.RT_SCHED_CURRENT), ("lagged", rt.RT_SCHED_LAGGED)):
+        arr = rt.CameraArray(wl.cams, flags=rt.RT_FLAG_THUMBNAILS | rt.RT_FLAG_SEAM_COST, schedule=sched)
+        logs, costs, preds = [], [], []
+        for t in range(frames):
+            arr.submit_frames(synth.frame_set(wl, t, device="cuda"), t)
+            maps, _ = arr.get_gains()
+            logs.append(np.log(maps[:, 0, 0, :, 0]))
+            costs.append(float(np.mean([c for (_, _, c) in arr.seam_costs()])))
+            if sched == rt.RT_SCHED_CURRENT:
+                p, _ = arr.surrogate_predict(net)
+                preds.append(np.log(p[:, 0, 0, :, 0]))
+        arr.close()
+        out[name] = {"gain_jitter": float(np.mean(np.abs(np.diff(np.stack(logs), axis=0)))),
+                     "seam_cost": float(np.mean(costs[1:]))}
+        if preds:
+            out["surrogate_raw_jitter"] = float(np.mean(np.abs(np.diff(np.stack(preds), axis=0))))
+    out["note"] = ("plain gains are the smoothed estimate (alpha 0.05); the surrogate's are its raw "
+                   "per-frame predictions (it is not applied inside the pipeline)")
+    return out
 
 
 # ---------------------------------------------------------------------------
