@@ -458,14 +458,15 @@ constexpr int kHistWords = 3 * 256 * kHistLanes;
 
 constexpr int kThumbWords = RT_THUMB_H * RT_THUMB_W * 3;
 
-// The thumbnail variants and the seam maps (per-column coefficients of both
-// rows of a unit in registers) get the registers of one CTA per SM.
+// The thumbnail variants get the registers of one CTA per SM, the seam maps
+// those of RT_PASS_B_SEAM_CTAS_PER_SM.
 template <int FIT, bool THUMBS>
-constexpr bool kOneCtaPerSm = THUMBS || FIT != RT_FIT_GLOBAL;
+constexpr int kMaxThreads = THUMBS ? 512 : (FIT == RT_FIT_GLOBAL ? RT_PASS_B_THREADS : RT_PASS_B_SEAM_THREADS);
+template <int FIT, bool THUMBS>
+constexpr int kMinCtas = THUMBS ? 1 : (FIT == RT_FIT_GLOBAL ? RT_PASS_B_CTAS_PER_SM : RT_PASS_B_SEAM_CTAS_PER_SM);
 
 template <int FIT, bool STATS, bool THUMBS>
-__global__ void __launch_bounds__(kOneCtaPerSm<FIT, THUMBS> ? 512 : RT_PASS_B_THREADS,
-                                  kOneCtaPerSm<FIT, THUMBS> ? 1 : RT_PASS_B_CTAS_PER_SM)
+__global__ void __launch_bounds__(kMaxThreads<FIT, THUMBS>, kMinCtas<FIT, THUMBS>)
 pass_b_kernel(const ArrayGeom g, const PassBArgs a)
 {
     extern __shared__ uint32_t sh[];
@@ -576,8 +577,7 @@ template <int FIT, bool STATS, bool THUMBS>
 cudaError_t launch_one(const ArrayGeom &g, const PassBArgs &a, int grid, int threads, cudaStream_t s)
 {
     const size_t smem = (size_t)((STATS ? kHistWords : 0) + (THUMBS ? kThumbWords : 0)) * 4;
-    // the one-CTA-per-SM variants are compiled for at most 512 threads per CTA
-    if (kOneCtaPerSm<FIT, THUMBS> && threads > 512) threads = 512;
+    if (threads > kMaxThreads<FIT, THUMBS>) threads = kMaxThreads<FIT, THUMBS>;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(threads);

@@ -744,8 +744,9 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     if (h->seams && dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_seam[ev2], 0));
     if (prof) RT_CUDA(h, prof_record(h, pe.b0, h->s_main));
     // the thumbnail variant with frame statistics needs the shared memory of
-    // one CTA per SM, the seam maps its registers
-    const int pb_grid = ((fh && th) || p.fit_mode != RT_FIT_GLOBAL) ? h->sm_count : h->pb_grid;
+    // one CTA per SM; the seam maps run their own number per SM
+    const int pb_grid = (fh && th) ? h->sm_count
+                        : p.fit_mode != RT_FIT_GLOBAL ? h->sm_count * RT_PASS_B_SEAM_CTAS_PER_SM : h->pb_grid;
     RT_CUDA(h, launch_pass_b(g, pb, pb_grid, h->pb_threads, h->pb_smem, h->s_main));
     if (prof) RT_CUDA(h, prof_record(h, pe.b1, h->s_main));
     const bool from_props = n_crops == RT_CROPS_FROM_PROPOSALS;

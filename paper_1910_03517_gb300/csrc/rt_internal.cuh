@@ -32,6 +32,16 @@ namespace rt {
 #define RT_PASS_B_RUN_THREADS 384
 #endif
 
+// The seam-map variants of pass B (per-column coefficients of both rows of a
+// unit in registers) run RT_PASS_B_SEAM_CTAS_PER_SM CTAs of at most
+// RT_PASS_B_SEAM_THREADS threads per SM.
+#ifndef RT_PASS_B_SEAM_THREADS
+#define RT_PASS_B_SEAM_THREADS 512
+#endif
+#ifndef RT_PASS_B_SEAM_CTAS_PER_SM
+#define RT_PASS_B_SEAM_CTAS_PER_SM 1
+#endif
+
 constexpr int kUnitCols = 16;          // columns a thread converts per row
 
 // Values of one (camera, side, block) map: 3 channels x (a, b), or a 3 x 3
