@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-track", action="store_true", help="skip the NMS / tracker report")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--attention", action="store_true", help="also run the difference attention (off by default)")
     ap.add_argument("--seam-cost", action="store_true", help="also compute the per-seam cost (off by default)")
@@ -368,6 +369,112 @@ def surrogate_report(args):
     }
 
 
+def detection_frames(frames=60, n_obj=200, classes=8, seed=21):
+    """Synthetic detector output over a 14-camera panorama (26880 x 1080):
+    objects moving a few pixels a frame, three jittered detections each (what
+    NMS removes), objects appearing and leaving, spurious low boxes.  Rows
+    (x0, y0, x1, y1, score, category)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform([0, 100], [26000, 900], (n_obj, 2))
+    size = rng.uniform(16, 120, (n_obj, 2))
+    vel = rng.uniform(-8, 8, (n_obj, 2))
+    cls = rng.integers(0, classes, n_obj)
+    life = np.stack([rng.integers(0, frames // 2, n_obj), rng.integers(frames // 2, frames + 1, n_obj)], 1)
+    out = []
+    for f in range(frames):
+        rows = []
+        for i in range(n_obj):
+            if not (life[i, 0] <= f < life[i, 1]):
+                continue
+            c = pos[i] + vel[i] * f
+            for _ in range(3):
+                j = rng.normal(0, 2.0, 4)
+                rows.append((c[0] + j[0], c[1] + j[1], c[0] + size[i, 0] + j[2], c[1] + size[i, 1] + j[3],
+                             float(rng.uniform(0.6, 1.0)), int(cls[i])))
+        for _ in range(int(rng.integers(10, 40))):
+            c = rng.uniform([0, 0], [26800, 1050])
+            rows.append((c[0], c[1], c[0] + 30, c[1] + 30, float(rng.uniform(0.1, 0.7)), int(rng.integers(0, classes))))
+        out.append(rows)
+    return out
+
+
+def track_report(oracle_seconds=6.0):
+    """Detection post-processing (greedy per-category NMS on the GPU) and the
+    assignment tracker (host code) per frame through the C ABI, against the
+    oracle's on the host cores over the same frames (timed up to
+    `oracle_seconds`); keep lists and object ids compared."""
+    import ctypes
+    import numpy as np
+    from paper_1910_03517_gb300 import rt
+    L = rt.load()
+    rt._load_track(L)
+    import torch
+    frames = detection_frames()
+    # boxes and keep flags in pinned host memory (asynchronous copies)
+    arrs, keep_t = [], []
+    for f in frames:
+        host = rt._boxes(f)
+        buf = torch.empty(ctypes.sizeof(host), dtype=torch.uint8).pin_memory()
+        ctypes.memmove(buf.data_ptr(), host, ctypes.sizeof(host))
+        arrs.append(buf)
+        keep_t.append(torch.zeros(len(f), dtype=torch.int32).pin_memory())
+    dev = [a.cuda() for a in arrs]
+    torch.cuda.synchronize()
+
+    def run_nms(src):
+        for i, f in enumerate(frames):
+            st = L.rt_nms(ctypes.c_void_p(src[i].data_ptr()), len(f), 0.65, 0.45,
+                          ctypes.c_void_p(keep_t[i].data_ptr()), None)
+            assert st == rt.RT_OK
+
+    run_nms(arrs)   # warm-up
+    t0 = time.perf_counter()
+    run_nms(arrs)
+    t_nms = (time.perf_counter() - t0) / len(frames)
+    t0 = time.perf_counter()
+    run_nms(dev)
+    t_nms_dev = (time.perf_counter() - t0) / len(frames)
+    keeps = [k.numpy() for k in keep_t]
+    kept = [[r for r, k in zip(f, keeps[i]) if k] for i, f in enumerate(frames)]
+    karrs = [rt._boxes(k) for k in kept]
+    ids = [np.zeros(max(1, len(k)), np.int32) for k in kept]
+    tr = ctypes.c_void_p()
+    assert L.rt_tracker_create(ctypes.byref(tr), 0.99, 0.05, 0.001) == rt.RT_OK
+    t0 = time.perf_counter()
+    for i, k in enumerate(kept):
+        assert L.rt_tracker_update(tr, ctypes.cast(karrs[i], ctypes.c_void_p), len(k), i, ids[i].ctypes.data) == rt.RT_OK
+    t_trk = (time.perf_counter() - t0) / len(frames)
+    L.rt_tracker_destroy(tr)
+    # the oracle on the host cores (the cpu baseline of this row), same frames
+    from oracle import track as otrack
+    f32 = [[tuple(float(np.float32(v)) for v in r[:5]) + (int(r[5]),) for r in f] for f in frames]
+    n_or, t_or_nms, t_or_trk, same = 0, 0.0, 0.0, True
+    otr = otrack.Tracker()
+    while n_or < len(frames) and t_or_nms + t_or_trk < oracle_seconds:
+        t0 = time.perf_counter()
+        keep_or = otrack.nms(f32[n_or], 0.65, 0.45)
+        t_or_nms += time.perf_counter() - t0
+        same = same and sorted(keep_or) == [j for j, k in enumerate(keeps[n_or]) if k]
+        kf = [f32[n_or][j] for j in sorted(keep_or)]
+        t0 = time.perf_counter()
+        ids_or = otr.update(kf, n_or)
+        t_or_trk += time.perf_counter() - t0
+        same = same and list(ids_or) == [int(x) for x in ids[n_or][:len(kf)]]
+        n_or += 1
+    n_boxes = float(np.mean([len(f) for f in frames]))
+    return {"frames": len(frames), "boxes_per_frame": round(n_boxes, 1),
+            "kept_per_frame": round(float(np.mean([len(k) for k in kept])), 1),
+            "nms_us_per_frame": round(1e6 * t_nms, 1), "nms_device_boxes_us_per_frame": round(1e6 * t_nms_dev, 1),
+            "tracker_us_per_frame": round(1e6 * t_trk, 1),
+            "note": "rt_nms: boxes from pinned host (or device) memory, keep flags back to pinned host memory, "
+                    "one synchronous call per frame",
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "frames": n_or,
+                             "nms_us_per_frame": round(1e6 * t_or_nms / max(1, n_or), 1),
+                             "tracker_us_per_frame": round(1e6 * t_or_trk / max(1, n_or), 1),
+                             "same_keep_and_ids": bool(same)}}
+
+
 def quality_sequence(net, n_cams, W, H, frames=30):
     """A moving object crossing seams, camera gains drifting 1 % a frame:
     frame-to-frame jitter of the log-gains (mean |ln g_t - ln g_{t-1}| over
@@ -557,6 +664,7 @@ def run_ours(args):
     sur = None
     if rank == 0 and not args.no_surrogate:
         sur = surrogate_report(args)
+    trk = track_report() if rank == 0 and not args.no_track else None
     if rank == 0:
         ring_desc = "ring of %d distinct input frame sets (%.0f MB) > 4x L2 (%.0f MB); outputs double buffered" % (
             ring, ring * in_bytes / 1e6, l2 / 1e6)
@@ -583,6 +691,7 @@ def run_ours(args):
             "clocks": ck,
             "tuning": tuning,
             "surrogate": sur,
+            "detections": trk,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -28,7 +28,8 @@ typedef struct {
  * suppressed, until none remains; equal probabilities keep the earlier box.
  * boxes: n boxes in host or device memory (1 <= n <= 4096); keep: n int32 in
  * host memory, 1 for a kept box, 0 otherwise.  Runs on cuda_stream (NULL:
- * the default stream) and returns when done.  RT_ERR_INVALID for a bad n, a
+ * the default stream) and returns when done; allocates nothing (calls from
+ * several threads run one at a time).  RT_ERR_INVALID for a bad n, a
  * NULL pointer or a category outside 0..32767; RT_ERR_CUDA on a CUDA error. */
 rt_status rt_nms(const rt_box *boxes, int32_t n, float score_min, float iou_max, int32_t *keep, void *cuda_stream);
 

@@ -1,10 +1,13 @@
 // Detection post-processing and tracking (Sec. "AI-based video tracking").
 //
-// rt_nms: one CTA sorts the boxes by (valid first, category, probability
-// descending, index) with a bitonic sort in shared memory, then walks them
-// in that order: a box still alive is kept and, all threads at once, kills
-// the later boxes of its category (a contiguous range after the sort) whose
-// IoU with it exceeds the tolerance.
+// rt_nms: one CTA stages the boxes in shared memory, sorts them by (valid
+// first, category, probability descending, index) with a bitonic sort; each
+// category is then a contiguous run, walked greedily by one warp (runs of
+// different categories in parallel): a box still alive is kept and the
+// warp's lanes kill the later boxes of the run whose IoU with it exceeds
+// the tolerance.  The device copies of
+// the boxes and flags live in a static device array (calls are serialised
+// by a host mutex): no allocation per call.
 //
 // rt_tracker: host code -- the assignment problems are a few dozen rows.
 // The linear sum assignment is the Hungarian method with row and column
@@ -12,6 +15,7 @@
 // R <= C rows), run per category.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "rt_internal.cuh"
@@ -23,6 +27,10 @@ namespace {
 
 constexpr int kNmsMax = 4096;
 constexpr int kNmsThreads = 1024;
+
+__device__ rt_box g_nms_boxes[kNmsMax];
+__device__ int32_t g_nms_keep[kNmsMax];
+std::mutex g_nms_mutex;
 
 __device__ __forceinline__ float box_iou(const rt_box &a, const rt_box &b)
 {
@@ -36,16 +44,22 @@ __device__ __forceinline__ float box_iou(const rt_box &a, const rt_box &b)
 __global__ void __launch_bounds__(kNmsThreads) nms_kernel(const rt_box *__restrict__ boxes, int n, float smin,
                                                           float thr, int32_t *__restrict__ keep)
 {
-    extern __shared__ unsigned long long key[];          // [n2]
+    extern __shared__ unsigned long long key[];          // [n2], then the boxes [n]
     __shared__ uint8_t dead[kNmsMax];
+    __shared__ int run_start[kNmsMax];
+    __shared__ int n_runs;
     int n2 = 1;
     while (n2 < n) n2 <<= 1;
-    const int tid = threadIdx.x;
+    rt_box *sbox = reinterpret_cast<rt_box *>(key + n2);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    if (tid == 0) n_runs = 0;
+    for (int i = tid; i < n; i += blockDim.x) sbox[i] = boxes[i];
+    __syncthreads();
     // key: bit 63 invalid, bits 48..62 category, bits 16..47 ~(probability bits), bits 0..15 index
     for (int i = tid; i < n2; i += blockDim.x) {
         unsigned long long k = ~0ull;
         if (i < n) {
-            const rt_box b = boxes[i];
+            const rt_box b = sbox[i];
             const bool valid = b.score >= smin && b.score >= 0.0f;
             const uint32_t sb = __float_as_uint(fmaxf(b.score, 0.0f));
             k = ((unsigned long long)(valid ? 0u : 1u) << 63) | ((unsigned long long)(b.cls & 0x7FFF) << 48) |
@@ -67,20 +81,34 @@ __global__ void __launch_bounds__(kNmsThreads) nms_kernel(const rt_box *__restri
             }
             __syncthreads();
         }
-    for (int i = tid; i < n2; i += blockDim.x) dead[i] = (key[i] >> 63) ? 1 : 0;
+    // runs of one category among the valid boxes (contiguous after the sort)
+    for (int i = tid; i < n; i += blockDim.x) {
+        dead[i] = 0;
+        const unsigned long long k = key[i];
+        if (!(k >> 63) && (i == 0 || (key[i - 1] >> 48) != (k >> 48))) run_start[atomicAdd(&n_runs, 1)] = i;
+    }
     __syncthreads();
-    for (int p = 0; p < n; ++p) {
-        if (dead[p]) continue;                            // uniform: all threads read the same byte
-        const unsigned long long kp = key[p];
-        const rt_box bp = boxes[kp & 0xFFFF];
-        const uint32_t cp = (uint32_t)(kp >> 48) & 0x7FFFu;
-        if (tid == 0) keep[kp & 0xFFFF] = 1;
-        for (int q = p + 1 + tid; q < n; q += blockDim.x) {
-            const unsigned long long kq = key[q];
-            if ((kq >> 63) || (((uint32_t)(kq >> 48) & 0x7FFFu) != cp) || dead[q]) continue;
-            if (box_iou(bp, boxes[kq & 0xFFFF]) > thr) dead[q] = 1;
+    // one warp per category run: the greedy walk needs only warp barriers
+    for (int r = warp; r < n_runs; r += nwarps) {
+        const int s = run_start[r];
+        const unsigned long long cat = key[s] >> 48;
+        int e = s + 1;
+        while (true) {   // end of the run: the first later key of another category (or invalid)
+            const int q = e + lane;
+            const bool other = q >= n || (key[q] >> 48) != cat;
+            const unsigned m = __ballot_sync(0xffffffffu, other);
+            if (m) { e += __ffs(m) - 1; break; }
+            e += 32;
         }
-        __syncthreads();
+        for (int p = s; p < e; ++p) {
+            if (dead[p]) continue;                        // uniform across the warp
+            const unsigned long long kp = key[p];
+            const rt_box bp = sbox[kp & 0xFFFF];
+            if (lane == 0) keep[kp & 0xFFFF] = 1;
+            for (int q = p + 1 + lane; q < e; q += 32)
+                if (!dead[q] && box_iou(bp, sbox[key[q] & 0xFFFF]) > thr) dead[q] = 1;
+            __syncwarp();
+        }
     }
 }
 
@@ -163,22 +191,28 @@ rt_status rt_nms(const rt_box *boxes, int32_t n, float score_min, float iou_max,
     if (!on_device)
         for (int i = 0; i < n; ++i)
             if (boxes[i].cls < 0 || boxes[i].cls > 32767) return RT_ERR_INVALID;
-    rt_box *d_boxes = nullptr;
-    int32_t *d_keep = nullptr;
-    cudaError_t e = cudaMalloc(&d_boxes, sizeof(rt_box) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&d_keep, sizeof(int32_t) * n);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_boxes, boxes, sizeof(rt_box) * n, cudaMemcpyDefault, st);
     int n2 = 1;
     while (n2 < n) n2 <<= 1;
+    const size_t smem = sizeof(unsigned long long) * n2 + sizeof(rt_box) * n;   // <= 32 KB + 96 KB
+    static bool smem_set = false;
+    cudaError_t e = cudaSuccess;
+    if (!smem_set) {
+        e = cudaFuncSetAttribute(rt::nms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(unsigned long long) * rt::kNmsMax + sizeof(rt_box) * rt::kNmsMax));
+        smem_set = e == cudaSuccess;
+    }
+    std::lock_guard<std::mutex> lock(rt::g_nms_mutex);
+    rt_box *d_boxes = nullptr;
+    int32_t *d_keep = nullptr;
+    if (e == cudaSuccess) e = cudaGetSymbolAddress((void **)&d_boxes, rt::g_nms_boxes);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress((void **)&d_keep, rt::g_nms_keep);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_boxes, boxes, sizeof(rt_box) * n, cudaMemcpyDefault, st);
     if (e == cudaSuccess) {
-        rt::nms_kernel<<<1, rt::kNmsThreads, sizeof(unsigned long long) * n2, st>>>(d_boxes, n, score_min, iou_max,
-                                                                                  d_keep);
+        rt::nms_kernel<<<1, rt::kNmsThreads, smem, st>>>(d_boxes, n, score_min, iou_max, d_keep);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(keep, d_keep, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(d_boxes);
-    cudaFree(d_keep);
     return e == cudaSuccess ? RT_OK : RT_ERR_CUDA;
 }
 
