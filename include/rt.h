@@ -312,8 +312,9 @@ typedef struct {
     int32_t pass_b_ctas_per_sm;  /* 1 or 2 (the thumbnail variant always runs 1) */
     int32_t pass_a_rows;         /* rows per band-statistics work item, 8..1024 */
     int32_t pass_a_threads;      /* threads per band-statistics CTA: 64, 128 or 256 */
-    int32_t crop_threads;        /* threads per crop CTA: 128 or 256 */
-    int32_t crop_grid;           /* at most this many CTAs per crop window, 1..4096 */
+    int32_t crop_threads;        /* threads per crop CTA, 128 or 256 (crops over 2048 pixels a
+                                    side; smaller ones run crop_size / 2 threads a CTA) */
+    int32_t crop_grid;           /* at most this many CTAs per crop window, 1..4096 (row groups) */
     double step_us;              /* rt_autotune: measured time per frame set of this shape */
     int32_t from_cache;          /* rt_autotune: 1 if the shape came from the cache file */
     int32_t candidates;          /* rt_autotune: shapes timed (0 when cached) */

@@ -120,12 +120,109 @@ __global__ void __launch_bounds__(256) crops_kernel(const ArrayGeom g, const Cro
     }
 }
 
+// Column-stationary variant: a thread owns one output pixel pair column
+// (blockDim = pairs per row) and walks the rows blockIdx.x, +gridDim.x, ...;
+// the columns' taps, weights and load alignment are set up once.  The
+// arithmetic is the row-major kernel's, operation for operation.
+struct ColTap {
+    int aoff;          // byte offset of the aligned 4-byte word holding the left tap
+    uint32_t sh;       // funnel shift of the 6 tap bytes within the words
+    uint32_t wq;       // Q15 weights
+};
+
+__device__ __forceinline__ ColTap col_tap(float sxs, int w, float x, uintptr_t base_mod4)
+{
+    const float fx = fminf(fmaxf(fmaf(x + 0.5f, sxs, -0.5f), 0.0f), (float)(w - 1));
+    float wx;
+    const int xlo = floor_frac(fx, wx);
+    const uint32_t w1 = (uint32_t)__float_as_int(fmaf(wx, 32768.0f, kTwo23)) - 0x4B000000u;   // round(wx 2^15)
+    ColTap t;
+    t.wq = (32768u - w1) | (w1 << 16);
+    const int b = 3 * xlo;
+    const int mis = (int)((base_mod4 + (uintptr_t)b) & 3u);
+    t.aoff = b - mis;
+    t.sh = 8u * (uint32_t)mis;
+    return t;
+}
+
+// Horizontal lerp of one source row with a column's taps: three aligned
+// 4-byte loads hold the 6 tap bytes.
+__device__ __forceinline__ void row_lerp_col(const uint8_t *row, const ColTap &c, uint32_t (&t)[3])
+{
+    const uint32_t *q = reinterpret_cast<const uint32_t *>(row + c.aoff);
+    const uint32_t w0 = __ldg(q), w1 = __ldg(q + 1), w2 = __ldg(q + 2);
+    const uint32_t lo = __funnelshift_r(w0, w1, c.sh), hi = __funnelshift_r(w1, w2, c.sh);
+    const uint32_t rg = __byte_perm(lo, hi, 0x4130u);  // [Lr Rr Lg Rg]
+    const uint32_t bb = __byte_perm(lo, hi, 0x5252u);  // [Lb Rb . .]
+    t[0] = __dp2a_lo(c.wq, rg, 0u);
+    t[1] = __dp2a_hi(c.wq, rg, 0u);
+    t[2] = __dp2a_lo(c.wq, bb, 0u);
+}
+
+__global__ void __launch_bounds__(1024) crops_cols_kernel(const ArrayGeom g, const CropArgs a)
+{
+    const int n = blockIdx.y;
+    if (a.count && n >= *a.count) return;
+    const rt_crop cr = a.crops[n];
+    const CamGeom &cg = g.cam[cr.cam];
+    const int S = a.S;
+    const float sxs = (float)cr.w / (float)S, sys = (float)cr.h / (float)S;
+    const size_t plane = (size_t)S * S;
+    __half *out = a.out + (size_t)n * 3 * plane;
+    const uint8_t *base = cg.rgb + (size_t)cr.y0 * cg.rgb_pitch + 3 * cr.x0;
+    // rows start on 16 bytes: a row's byte alignment is the window base's
+    const uintptr_t bmod = reinterpret_cast<uintptr_t>(base) & 3u;
+    const float kScale = 1.0f / (255.0f * 32768.0f);
+    const int ox = 2 * (int)threadIdx.x;
+    const bool two = ox + 1 < S;
+    const float fox = int_f(ox);
+    const ColTap c0 = col_tap(sxs, cr.w, fox, bmod);
+    const ColTap c1 = col_tap(sxs, cr.w, fox + 1.0f, bmod);
+    for (int oy = blockIdx.x; oy < S; oy += gridDim.x) {
+        const float fy = fminf(fmaxf(fmaf(int_f(oy) + 0.5f, sys, -0.5f), 0.0f), (float)(cr.h - 1));
+        float wy;
+        const int ylo = floor_frac(fy, wy), yhi = min(ylo + 1, cr.h - 1);
+        const float s1 = wy * kScale, s0 = kScale - s1;
+        const uint8_t *r0 = base + (size_t)ylo * cg.rgb_pitch, *r1 = base + (size_t)yhi * cg.rgb_pitch;
+        uint32_t t[3], b[3];
+        float v0[3], v1[3];
+        row_lerp_col(r0, c0, t);
+        row_lerp_col(r1, c0, b);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v0[c] = fmaf(int_f((int)b[c]), s1, int_f((int)t[c]) * s0);
+        const size_t o = (size_t)oy * S + ox;
+        if (two) {
+            row_lerp_col(r0, c1, t);
+            row_lerp_col(r1, c1, b);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v1[c] = fmaf(int_f((int)b[c]), s1, int_f((int)t[c]) * s0);
+            if ((S & 1) == 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    *reinterpret_cast<__half2 *>(out + c * plane + o) = __floats2half2_rn(v0[c], v1[c]);
+                continue;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out[c * plane + o + 1] = __float2half_rn(v1[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out[c * plane + o] = __float2half_rn(v0[c]);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_crops(const ArrayGeom &g, const CropArgs &a, int threads, int max_grid, cudaStream_t s)
 {
     if (a.n <= 0) return cudaSuccess;
-    const int pairs = a.S * ((a.S + 1) / 2);
+    const int hp = (a.S + 1) / 2;
+    if (hp <= 1024) {
+        // column-stationary: one CTA of hp threads per group of rows
+        dim3 grid(a.S < max_grid ? a.S : max_grid, a.n);
+        crops_cols_kernel<<<grid, hp, 0, s>>>(g, a);
+        return cudaGetLastError();
+    }
+    const int pairs = a.S * hp;
     const int per = (pairs + threads - 1) / threads;
     dim3 grid(per < max_grid ? per : max_grid, a.n);
     crops_kernel<<<grid, threads, 0, s>>>(g, a);

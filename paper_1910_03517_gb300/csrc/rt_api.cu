@@ -1544,8 +1544,12 @@ rt_status rt_autotune(rt_handle *h, int32_t n_sets, const void *const *y_planes,
     // stage 3: crops
     if (s == RT_OK && any_crops) {
         const rt_tuning base = best;
+        // crops up to 2048 pixels a side run one CTA of crop_size / 2 threads
+        // per group of rows: only the grid cap matters for them
+        const bool thr_matters = h->p.crop_size > 2048;
         for (int thr : {128, 256})
             for (int grid : {64, 256, 1024}) {
+                if (!thr_matters && thr != base.crop_threads) continue;
                 rt_tuning c = base;
                 c.crop_threads = thr;
                 c.crop_grid = grid;
