@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(256) crops_kernel(const ArrayGeom g, const Cro
 }
 
 // Column-stationary variant: a thread owns one output pixel pair column
-// (blockDim = pairs per row) and walks the rows blockIdx.x, +gridDim.x, ...;
+// (blockDim = pairs per row) and walks the rows blockIdx.x, +gridDim.x, ...,
+// two rows a round so that both rows' tap loads are in flight together;
 // the columns' taps, weights and load alignment are set up once.  The
 // arithmetic is the row-major kernel's, operation for operation.
 struct ColTap {
@@ -178,35 +179,56 @@ __global__ void __launch_bounds__(1024) crops_cols_kernel(const ArrayGeom g, con
     const float fox = int_f(ox);
     const ColTap c0 = col_tap(sxs, cr.w, fox, bmod);
     const ColTap c1 = col_tap(sxs, cr.w, fox + 1.0f, bmod);
-    for (int oy = blockIdx.x; oy < S; oy += gridDim.x) {
-        const float fy = fminf(fmaxf(fmaf(int_f(oy) + 0.5f, sys, -0.5f), 0.0f), (float)(cr.h - 1));
-        float wy;
-        const int ylo = floor_frac(fy, wy), yhi = min(ylo + 1, cr.h - 1);
-        const float s1 = wy * kScale, s0 = kScale - s1;
-        const uint8_t *r0 = base + (size_t)ylo * cg.rgb_pitch, *r1 = base + (size_t)yhi * cg.rgb_pitch;
-        uint32_t t[3], b[3];
-        float v0[3], v1[3];
-        row_lerp_col(r0, c0, t);
-        row_lerp_col(r1, c0, b);
+    // two rows per round: both rows' tap loads are in flight together
+    const int step = (int)gridDim.x;
+    for (int oy0 = blockIdx.x; oy0 < S; oy0 += 2 * step) {
+        const bool has_b = oy0 + step < S;
+        float s0[2], s1[2];
+        const uint8_t *ra[2], *rb[2];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) v0[c] = fmaf(int_f((int)b[c]), s1, int_f((int)t[c]) * s0);
-        const size_t o = (size_t)oy * S + ox;
-        if (two) {
-            row_lerp_col(r0, c1, t);
-            row_lerp_col(r1, c1, b);
+        for (int h = 0; h < 2; ++h) {
+            const int oy = h == 0 || !has_b ? oy0 : oy0 + step;
+            const float fy = fminf(fmaxf(fmaf(int_f(oy) + 0.5f, sys, -0.5f), 0.0f), (float)(cr.h - 1));
+            float wy;
+            const int ylo = floor_frac(fy, wy), yhi = min(ylo + 1, cr.h - 1);
+            s1[h] = wy * kScale;
+            s0[h] = kScale - s1[h];
+            ra[h] = base + (size_t)ylo * cg.rgb_pitch;
+            rb[h] = base + (size_t)yhi * cg.rgb_pitch;
+        }
+        uint32_t t[2][2][3], b[2][2][3];   // [row][pixel][channel]
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v1[c] = fmaf(int_f((int)b[c]), s1, int_f((int)t[c]) * s0);
-            if ((S & 1) == 0) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    *reinterpret_cast<__half2 *>(out + c * plane + o) = __floats2half2_rn(v0[c], v1[c]);
-                continue;
+        for (int h = 0; h < 2; ++h) {
+            row_lerp_col(ra[h], c0, t[h][0]);
+            row_lerp_col(rb[h], c0, b[h][0]);
+            if (two) {
+                row_lerp_col(ra[h], c1, t[h][1]);
+                row_lerp_col(rb[h], c1, b[h][1]);
             }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) out[c * plane + o + 1] = __float2half_rn(v1[c]);
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) out[c * plane + o] = __float2half_rn(v0[c]);
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !has_b) break;
+            const int oy = oy0 + h * step;
+            float v0[3], v1[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v0[c] = fmaf(int_f((int)b[h][0][c]), s1[h], int_f((int)t[h][0][c]) * s0[h]);
+            const size_t o = (size_t)oy * S + ox;
+            if (two) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v1[c] = fmaf(int_f((int)b[h][1][c]), s1[h], int_f((int)t[h][1][c]) * s0[h]);
+                if ((S & 1) == 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        *reinterpret_cast<__half2 *>(out + c * plane + o) = __floats2half2_rn(v0[c], v1[c]);
+                    continue;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[c * plane + o + 1] = __float2half_rn(v1[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out[c * plane + o] = __float2half_rn(v0[c]);
+        }
     }
 }
 
