@@ -320,13 +320,14 @@ def test_host_outputs_pipelined(rt):
     b.close()
 
 
-def test_state_save_and_resume(rt, orc):
+@pytest.mark.parametrize("fit_mode", [1, 3])
+def test_state_save_and_resume(rt, orc, fit_mode):
     wl = synth.small_pair()
-    a = rt.CameraArray(wl.cams, fit_mode=1, num_blocks=4)
+    a = rt.CameraArray(wl.cams, fit_mode=fit_mode, num_blocks=4)
     for t in range(3):
         a.submit_frames(synth.frame_set(wl, t, device="cuda"), t)
     blob = a.save_state()
-    b = rt.CameraArray(wl.cams, fit_mode=1, num_blocks=4)
+    b = rt.CameraArray(wl.cams, fit_mode=fit_mode, num_blocks=4)
     b.load_state(blob)
     for t in range(3, 6):
         fs = synth.frame_set(wl, t, device="cuda")
