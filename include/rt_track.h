@@ -30,7 +30,9 @@ typedef struct {
  * host memory, 1 for a kept box, 0 otherwise.  Runs on cuda_stream (NULL:
  * the default stream) and returns when done; allocates nothing (calls from
  * several threads run one at a time).  RT_ERR_INVALID for a bad n, a
- * NULL pointer or a category outside 0..32767; RT_ERR_CUDA on a CUDA error. */
+ * NULL pointer or (boxes in host memory) a category outside 0..32767; the
+ * category of a box in device memory is taken modulo 32768.  RT_ERR_CUDA on
+ * a CUDA error. */
 rt_status rt_nms(const rt_box *boxes, int32_t n, float score_min, float iou_max, int32_t *keep, void *cuda_stream);
 
 typedef struct rt_tracker rt_tracker;

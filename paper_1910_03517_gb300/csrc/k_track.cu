@@ -194,14 +194,17 @@ rt_status rt_nms(const rt_box *boxes, int32_t n, float score_min, float iou_max,
     int n2 = 1;
     while (n2 < n) n2 <<= 1;
     const size_t smem = sizeof(unsigned long long) * n2 + sizeof(rt_box) * n;   // <= 32 KB + 96 KB
-    static bool smem_set = false;
-    cudaError_t e = cudaSuccess;
-    if (!smem_set) {
+    std::lock_guard<std::mutex> lock(rt::g_nms_mutex);
+    // the kernel's shared-memory limit, once per device
+    static bool smem_set[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && (dev < 0 || dev >= 64)) e = cudaErrorInvalidDevice;
+    if (e == cudaSuccess && !smem_set[dev]) {
         e = cudaFuncSetAttribute(rt::nms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(unsigned long long) * rt::kNmsMax + sizeof(rt_box) * rt::kNmsMax));
-        smem_set = e == cudaSuccess;
+        smem_set[dev] = e == cudaSuccess;
     }
-    std::lock_guard<std::mutex> lock(rt::g_nms_mutex);
     rt_box *d_boxes = nullptr;
     int32_t *d_keep = nullptr;
     if (e == cudaSuccess) e = cudaGetSymbolAddress((void **)&d_boxes, rt::g_nms_boxes);
