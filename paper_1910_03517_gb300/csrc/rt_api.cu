@@ -33,7 +33,7 @@ namespace {
 constexpr int kEvRing = 4;
 constexpr int kQRing = 3;
 #ifndef RT_STRIP_ROWS
-#define RT_STRIP_ROWS 32
+#define RT_STRIP_ROWS 64
 #endif
 constexpr int kStripRows = RT_STRIP_ROWS;   // rows of one pass-A work item
 constexpr uint32_t kStateMagic = 0x52545331u;
@@ -134,7 +134,7 @@ struct rt_handle {
     bool prof_branch[3] = {false, false, false};   // the capture in progress used s_prof[i]
     // launch shapes (rt_autotune / rt_set_tuning)
     int pb_grid = 0, pb_threads = RT_PASS_B_RUN_THREADS, pb_ctas = RT_PASS_B_CTAS_PER_SM;
-    int pa_rows = kStripRows, pa_threads = 64, crop_threads = 256, crop_grid = 64;
+    int pa_rows = kStripRows, pa_threads = 128, crop_threads = 256, crop_grid = 64;
     rt_tuning tuned{};
     size_t pb_smem = 0;
     std::string err;
