@@ -67,6 +67,8 @@ def _config(L, cams, **kw):
     ((640, 480, 0, 8, 640, 640, 0, 0), {"strip_width": 24}, "strip_width"),
     ((640, 480, 0, 8, 640, 640, 0, 0), {"alpha": 0.0}, "alpha"),
     ((640, 480, 0, 8, 640, 640, 0, 0), {"fit_mode": 7}, "fit_mode"),
+    ((640, 480, 0, 8, 640, 640, 0, 0), {"fit_mode": 4}, "fit_mode"),
+    ((640, 480, 0, 8, 640, 640, 0, 0), {"gain_max": 17.0}, "gain_max"),
     ((640, 480, 0, 8, 640, 640, 0, 0), {"max_crops": 4, "crop_size": 0}, "crop_size"),
 ])
 def test_invalid_configs_are_rejected(L, cam, kw, needle):
@@ -90,3 +92,23 @@ def test_null_handle_calls_are_invalid(L):
     assert L.rt_sync(None, 0) == rt.RT_ERR_INVALID
     assert L.rt_get_gains(None, None, None, 0, 0) == rt.RT_ERR_INVALID
     L.rt_destroy(None)
+
+
+@pytest.mark.parametrize("fit_mode", [0, 1, 2, 3])
+def test_every_fit_mode_passes_validation(L, fit_mode):
+    """The four fits are accepted by the checks made before any device
+    work (without a GPU the call then fails on the device, not on them)."""
+    from paper_1910_03517_gb300 import rt
+    p = rt.default_params()
+    cams = (rt.CameraDesc * 2)(rt.CameraDesc(640, 480, 0, 8, 640, 640, 0, 0),
+                               rt.CameraDesc(640, 480, 0, 8, 640, 640, 0, 1))
+    p.num_cameras = 2
+    p.cams = ctypes.cast(cams, ctypes.POINTER(rt.CameraDesc))
+    p.fit_mode = fit_mode
+    p.num_blocks = 1 if fit_mode == 0 else 16
+    h = ctypes.c_void_p()
+    st = L.rt_array_config(ctypes.byref(p), None, ctypes.byref(h))
+    if st == rt.RT_OK:
+        L.rt_destroy(h)
+    else:
+        assert st != rt.RT_ERR_INVALID, L.rt_last_error(None).decode()
