@@ -659,6 +659,11 @@ def run_ours(args):
         v, desc, el = time_oracle(wl, args, args.cpu_seconds, threads)
         cpu = {"value": v, "unit": "Mpix/s", "cores": threads, "kind": "oracle", "sample": desc,
                "seconds": round(el, 2)}
+        try:
+            v1, desc1, el1 = time_oracle(wl, args, min(5.0, args.cpu_seconds), 1)
+            cpu["single_thread"] = {"value": v1, "cores": 1, "sample": desc1, "seconds": round(el1, 2)}
+        except Exception as exc:   # the single-thread figure is context only
+            cpu["single_thread"] = {"error": repr(exc)}
 
     arr.close()
     sur = None
