@@ -4,8 +4,10 @@ joint band statistics against a numpy brute force, the moment-matching
 identity M S M^T = S_s with S_s the covariance of the pooled pixels, the
 pooled mean, symmetry and the eigenvalue clamp, the per-channel closed form
 for diagonal covariances, identity for equal bands, and the apply against the
-pinned affine apply (diagonal M) and against channel permutations."""
+pinned affine apply (diagonal M) and against channel permutations; and the
+whole fit against the definition evaluated with 40 significant digits."""
 import numpy as np
+import pytest
 
 from oracle import core
 
@@ -196,3 +198,58 @@ def test_step_runs_matrix_mode_and_blending():
     o2.step(np_frames(synth.frame_set(wl, 0)))
     r2 = o2.step(np_frames(synth.frame_set(wl, 1)))
     assert np.array_equal(r2["maps"], r1["maps"])
+
+
+def test_matches_a_40_digit_evaluation():
+    """The oracle's FP64 eigen-decomposition route against the same
+    definition evaluated with 40 significant digits (mpmath), on generic,
+    luma-dominated and mono-like (rank one plus ridge) bands, with and
+    without an active eigenvalue clamp: within the FP64 parity bar."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+
+    def fn(A, f):
+        E, Q = mp.eigsy(A)
+        return Q * mp.diag([f(e) for e in E]) * Q.T
+
+    rng = np.random.default_rng(37)
+    for trial in range(12):
+        n = 2000
+        if trial % 3 == 0:
+            mix1, mix2 = rng.uniform(-12, 12, (3, 3)) + 14 * np.eye(3), rng.uniform(-12, 12, (3, 3)) + 14 * np.eye(3)
+            pR = _band(rng, n, rng.uniform(60, 190, 3), mix1)
+            pL = _band(rng, n, rng.uniform(60, 190, 3), mix2)
+        elif trial % 3 == 1:
+            pR = _band(rng, n, rng.uniform(60, 190, 3), np.ones((3, 3)) * rng.uniform(5, 30) + np.eye(3))
+            pL = _band(rng, n, rng.uniform(60, 190, 3), np.ones((3, 3)) * rng.uniform(5, 30) + np.eye(3))
+        else:
+            g1, g2 = rng.normal(0, rng.uniform(3, 30), (n, 1)), rng.normal(0, rng.uniform(3, 30), (n, 1))
+            pR = np.clip((np.repeat(g1, 3, 1) + rng.uniform(50, 200)).round(), 1, 254).astype(np.int64)
+            pL = np.clip((np.repeat(g2, 3, 1) + rng.uniform(50, 200)).round(), 1, 254).astype(np.int64)
+        gmin, gmax = (0.25, 4.0) if trial < 6 else (0.97, 1.02)
+        m = _fit(pR, pL, core.Params(fit_mode=core.FIT_MATRIX, min_valid=1, gain_min=gmin, gain_max=gmax))
+        # the definition in 40 digits, from the exact integer moments
+        qR, qL = _joint_of(pR), _joint_of(pL)
+
+        def moments(q):
+            nn = mp.mpf(int(q[0]))
+            mu = [mp.mpf(int(q[1 + i])) / nn for i in range(3)]
+            idx = {(0, 0): 4, (0, 1): 5, (0, 2): 6, (1, 1): 7, (1, 2): 8, (2, 2): 9}
+            S = mp.matrix(3, 3)
+            for i in range(3):
+                for j in range(3):
+                    S[i, j] = mp.mpf(int(q[idx[(min(i, j), max(i, j))]])) / nn - mu[i] * mu[j] + \
+                        (mp.mpf(core.MATRIX_RIDGE) if i == j else 0)
+            return mu, S
+
+        muR, SR = moments(qR)
+        muL, SL = moments(qL)
+        d = [muL[i] - muR[i] for i in range(3)]
+        Ss = (SL + SR) * mp.mpf(0.5) + mp.matrix([[d[i] * d[j] / 4 for j in range(3)] for i in range(3)])
+        for (k, side, S) in ((0, 1, SR), (1, 0, SL)):
+            h, hi = fn(S, mp.sqrt), fn(S, lambda x: 1 / mp.sqrt(x))
+            M = hi * fn(h * Ss * h, mp.sqrt) * hi
+            M = fn((M + M.T) * mp.mpf(0.5), lambda x: min(max(x, mp.mpf(gmin)), mp.mpf(gmax)))
+            want = np.array([[float(M[i, j]) for j in range(3)] for i in range(3)])
+            got = m[k, side, 0, :9].reshape(3, 3)
+            assert np.abs(got - want).max() <= 1e-6 * np.abs(want).max(), (trial, np.abs(got - want).max())
