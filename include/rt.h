@@ -388,9 +388,11 @@ rt_status rt_load_state(rt_handle *h, const void *buf, size_t len);
  * (cudaStream_t) and the call returns without waiting.
  * Limits (RT_ERR_INVALID beyond them): at most 16 cameras, 4 blocks, a band
  * width of 16 or 32, 2160 rows per camera.  Its working memory is one
- * 2.7 MB array inside librt.so that every GPU which loads the library holds
- * until the process exits.  The first call on a device looks up that
- * array's device address (make it before any stream capture on the device).
+ * 2.6 MB (2,632,704-byte) array inside librt.so that every GPU which loads
+ * the library holds until the process exits.  The first call on a device
+ * looks up that array's device address (make that first call before any
+ * stream capture on the device).  Nothing is copied from host memory: the
+ * work list and seam tables travel in a kernel's parameter block.
  * Every call uses the same array: calls whose work overlaps on the GPU race
  * with each other; the array keeps the last call's contents, and the
  * statistics part is cleared at the start of every call. */

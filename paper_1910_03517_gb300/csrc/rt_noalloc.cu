@@ -1,13 +1,16 @@
 // rt_fit_gains_noalloc: the per-camera gain fit of one frame set without any
-// allocation, for callers that cannot call cudaMalloc (an allocator-owned
-// process, a plug-in inside another framework's memory pool, code running
-// inside a CUDA-graph capture scope they do not own): the band statistics,
-// the work list and the seam tables live in one file-scope device array.
+// allocation, for callers that cannot call cudaMalloc (a process whose device
+// memory belongs to another allocator or is reserved up front, a plug-in that
+// must not grow the device footprint): the band statistics, the work list and
+// the seam tables live in one file-scope device array.
 //
 // The array is shared by every call in the process: calls that overlap on
 // the GPU (different streams, or the same array used before a previous call
 // finished) race on it.  Its contents persist between calls; the statistics
-// part is cleared at the start of every call.
+// part is cleared at the start of every call.  Nothing is copied from host
+// memory: the work list and the seam tables are written into the array by a
+// small set-up kernel from its by-value parameter block.
+#include <atomic>
 #include <cstring>
 
 #include "rt_internal.cuh"
@@ -38,23 +41,56 @@ constexpr size_t kOffTables = (kOffItems + kItemsBytes + 255) / 256 * 256;   // 
 constexpr int kTableInts = (kNaCams + 1) + kNaCams * 4;
 constexpr size_t kScratchBytes = (kOffTables + kTableInts * 4 + 255) / 256 * 256;
 
+static_assert(kScratchBytes == 2632704, "the documented size of the scratch array");
+
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// device address of the array, per device (looked up once, on first use)
+// device address of the array, per device (looked up once, on first use;
+// concurrent first calls store the same value)
 constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices] = {};
+std::atomic<void *> g_scratch_addr[kMaxDevices];
 
 rt_status scratch_for_current_device(void **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RT_ERR_CUDA;
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
+    void *p = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RT_ERR_CUDA;
-        g_scratch_addr[dev] = p;
+        g_scratch_addr[dev].store(p, std::memory_order_release);
     }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return RT_OK;
+}
+
+// What the set-up kernel needs to write the band work list and the seam
+// tables (by value, a few hundred bytes).
+struct NaSetup {
+    int32_t K, B;
+    int32_t H[kNaCams];
+    int32_t tables[kTableInts];
+};
+
+// Work items in the order the host counts them: camera, side, block, then
+// kNaItemRows-row pieces of the block; then the seam tables.
+__global__ void noalloc_setup_kernel(const NaSetup a, StripItem *__restrict__ items, int32_t *__restrict__ tab)
+{
+    if (threadIdx.x == 0) {
+        int n = 0;
+        for (int k = 0; k < a.K; ++k)
+            for (int side = 0; side < 2; ++side)
+                for (int j = 0; j < a.B; ++j) {
+                    const int H = a.H[k];
+                    const int r0 = (int)(((long long)j * H) / a.B), r1 = (int)(((long long)(j + 1) * H) / a.B);
+                    for (int r = r0; r < r1; r += kNaItemRows) {
+                        StripItem it;
+                        it.cam = (int16_t)k; it.side = (int16_t)side; it.block = (int16_t)j; it.pad = 0;
+                        it.row0 = r; it.row1 = r + kNaItemRows < r1 ? r + kNaItemRows : r1;
+                        items[n++] = it;
+                    }
+                }
+    }
+    for (int i = threadIdx.x; i < kTableInts; i += blockDim.x) tab[i] = a.tables[i];
 }
 
 }  // namespace
@@ -107,21 +143,20 @@ extern "C" rt_status rt_fit_gains_noalloc(const rt_camera_desc *cams, int32_t nu
         cg.nblk = B;
         if (cg.H > Hmax) Hmax = cg.H;
     }
-    // band work items and seam tables (host arrays on the stack, copied in)
-    StripItem items[kNaItems];
+    // band work items (counted here, written by the set-up kernel) and seam tables
+    NaSetup su;
+    memset(&su, 0, sizeof su);
+    su.K = K; su.B = B;
     int n_items = 0;
-    for (int k = 0; k < K; ++k)
-        for (int side = 0; side < 2; ++side)
-            for (int j = 0; j < B; ++j) {
-                const int H = cams[k].height;
-                const int r0 = (int)(((long long)j * H) / B), r1 = (int)(((long long)(j + 1) * H) / B);
-                for (int r = r0; r < r1; r += kNaItemRows) {
-                    StripItem &it = items[n_items++];
-                    it.cam = (int16_t)k; it.side = (int16_t)side; it.block = (int16_t)j; it.pad = 0;
-                    it.row0 = r; it.row1 = r + kNaItemRows < r1 ? r + kNaItemRows : r1;
-                }
-            }
-    int32_t tables[kTableInts];
+    for (int k = 0; k < K; ++k) {
+        su.H[k] = cams[k].height;
+        for (int j = 0; j < B; ++j) {
+            const int H = cams[k].height;
+            const int r0 = (int)(((long long)j * H) / B), r1 = (int)(((long long)(j + 1) * H) / B);
+            n_items += 2 * ((r1 - r0 + kNaItemRows - 1) / kNaItemRows);
+        }
+    }
+    int32_t *tables = su.tables;
     int32_t *gs = tables, *gm = tables + (kNaCams + 1), *ln = gm + kNaCams, *rn = ln + kNaCams, *hh = rn + kNaCams;
     int n_groups = 0, n_members = 0;
     gs[0] = 0;
@@ -146,9 +181,8 @@ extern "C" rt_status rt_fit_gains_noalloc(const rt_camera_desc *cams, int32_t nu
     }
     StripItem *d_items = reinterpret_cast<StripItem *>(base + kOffItems);
     int32_t *d_tab = reinterpret_cast<int32_t *>(base + kOffTables);
-    if (cudaMemcpyAsync(d_items, items, sizeof(StripItem) * n_items, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(d_tab, tables, sizeof tables, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return RT_ERR_CUDA;
+    noalloc_setup_kernel<<<1, 128, 0, st>>>(su, d_items, d_tab);
+    if (cudaGetLastError() != cudaSuccess) return RT_ERR_CUDA;
     // statistics start at zero
     if (cudaMemsetAsync(base + kOffHist, 0, kHistBytes, st) != cudaSuccess ||
         cudaMemsetAsync(base + kOffSum, 0, kSumBytes, st) != cudaSuccess)

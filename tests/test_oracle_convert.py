@@ -58,6 +58,45 @@ def test_all_triples_within_one_of_real_matrix(orc, matrix, kr, kb):
     assert np.mean(err <= 0.75) > 0.97
 
 
+# The published 8-bit integer forms of the two limited-range matrices
+# (coefficients scaled by 256): luma 298, then Cr->R, Cb->G, Cr->G, Cb->B.
+Q8 = {0: (298, 459, 55, 136, 541),      # ITU-R BT.709
+      1: (298, 409, 100, 208, 516)}     # ITU-R BT.601
+
+
+@pytest.mark.parametrize("matrix,kr,kb", [(0, 0.2126, 0.0722), (1, 0.299, 0.114)])
+def test_q8_integers_exact(orc, matrix, kr, kb):
+    """The oracle's integers are exactly the standard's Q8 matrix, and that
+    matrix follows from the luma weights (Kr, Kb) of the standard: 255/219
+    scales limited-range luma, 255/224 chroma, and the RGB rows are
+    R = Y' + 2(1-Kr) Cr', G = Y' - 2(1-Kb)Kb/Kg Cb' - 2(1-Kr)Kr/Kg Cr',
+    B = Y' + 2(1-Kb) Cb' (Kg = 1 - Kr - Kb)."""
+    kg = 1.0 - kr - kb
+    sy, sc = 256 * 255 / 219, 256 * 255 / 224
+    derived = (round(sy), round(sc * 2 * (1 - kr)), round(sc * 2 * (1 - kb) * kb / kg),
+               round(sc * 2 * (1 - kr) * kr / kg), round(sc * 2 * (1 - kb)))
+    assert derived == Q8[matrix]
+    assert tuple(int(v) for v in orc.color_coeffs(matrix)) == Q8[matrix]
+
+
+@pytest.mark.parametrize("matrix", [0, 1])
+def test_all_triples_exact_with_published_integers(orc, matrix):
+    """Every (Y, U, V) triple converts exactly as the published Q8 matrix
+    gives: v = clamp(floor(N / 256), 0, 255), N = 298 C + ... + 128 (C = Y - 16,
+    D = U - 128, E = V - 128).  A coefficient off by one (e.g. 460 for 459)
+    changes some triple's output and fails here."""
+    cy, crv, cgu, cgv, cbu = Q8[matrix]
+    y, uv = _all_triples_frame()
+    rgb, _ = orc.convert(synth.Camera(4096, 4096), {"y": y, "uv": uv}, matrix)
+    C = y.astype(np.int64) - 16
+    D = np.repeat(np.repeat(uv[:, 0::2], 2, 0), 2, 1).astype(np.int64) - 128
+    E = np.repeat(np.repeat(uv[:, 1::2], 2, 0), 2, 1).astype(np.int64) - 128
+    want = np.stack([(cy * C + crv * E + 128) // 256,
+                     (cy * C - cgu * D - cgv * E + 128) // 256,
+                     (cy * C + cbu * D + 128) // 256], -1)
+    assert np.array_equal(rgb, np.clip(want, 0, 255).astype(np.uint8))
+
+
 def test_range_end_points(orc):
     cam = synth.Camera(2, 2)
     for Y, want in [(235, 255), (16, 0), (255, 255), (0, 0)]:
