@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--ring", type=int, default=0, help="distinct input frame sets (multiple of 6)")
     ap.add_argument("--e2e-steps", type=int, default=120)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the uneven-array and 24x4K lines (run after the tower12 line)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-track", action="store_true", help="skip the NMS / tracker report")
@@ -511,6 +513,216 @@ def quality_sequence(net, n_cams, W, H, frames=30):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+MAX_GRAPH_SETS = 1200
+
+
+def graph_plan(K):
+    """(graph length L, launches, trailing single submits) covering exactly K
+    timed frame sets: one graph of K frame sets when K <= MAX_GRAPH_SETS, else
+    graphs of a multiple of 6 relaunched back to back (plus K mod 6 singles)."""
+    if K <= MAX_GRAPH_SETS:
+        return K, 1, 0
+    q, r = divmod(K, 6)
+    L = max(g for g in range(6, MAX_GRAPH_SETS + 1, 6) if (6 * q) % g == 0)
+    return L, 6 * q // L, r
+
+
+def ring_size(args, l2, in_bytes):
+    ring = args.ring or max(6, -(-int(4 * l2 / in_bytes + 1) // 6) * 6)
+    return max(6, ring - ring % 6)
+
+
+def crop_alg_bytes(crops, S):
+    """Algorithmic bytes of the crops of one frame set: every FP16 output value
+    written once (6 B per output pixel) and every source pixel the bilinear
+    taps touch read once (3 B of corrected RGB24)."""
+    import numpy as np
+    total = 0.0
+    o = (np.arange(S) + 0.5) / S
+    for (_, x0, y0, w, h) in crops:
+        def touched(n):
+            sx = np.clip(o * n - 0.5, 0.0, n - 1.0)
+            i0 = np.floor(sx).astype(np.int64)
+            return len(np.union1d(i0, np.minimum(i0 + 1, n - 1)))
+        total += 6.0 * S * S + 3.0 * touched(w) * touched(h)
+    return total
+
+
+def host_link_peaks(dev, nbytes=1 << 28, reps=5):
+    """Plain pinned cudaMemcpyAsync bandwidth (GB/s) host->device alone,
+    device->host alone, and both directions at once on two streams."""
+    import torch
+    hs = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    hd = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    da = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    db = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    cur = torch.cuda.current_stream(dev)
+
+    def best(h2d, d2h):
+        t = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            cur.synchronize()
+            e0.record(cur)
+            s1.wait_stream(cur)
+            s2.wait_stream(cur)
+            if h2d:
+                with torch.cuda.stream(s1):
+                    da.copy_(hs, non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s2):
+                    hd.copy_(db, non_blocking=True)
+            cur.wait_stream(s1)
+            cur.wait_stream(s2)
+            e1.record(cur)
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1) / 1e3)
+        return (int(h2d) + int(d2h)) * nbytes / min(t) / 1e9
+
+    best(True, True)   # warm-up
+    out = {"h2d": best(True, False), "d2h": best(False, True), "both": best(True, True),
+           "bytes_per_copy": nbytes}
+    del hs, hd, da, db
+    return out
+
+
+def measure(args, wl, K, W, dev, stream, autotune=True, timing_events="pass_b"):
+    """Throughput of the path on workload wl: W untimed warm-up frame sets,
+    then exactly K frame sets timed with CUDA events on the caller's stream,
+    all of them through captured graphs (graph_plan).  Returns a dict."""
+    import torch
+    from paper_1910_03517_gb300 import rt, synth
+
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    in_bytes = input_bytes(wl)
+    ring = ring_size(args, l2, in_bytes)
+    # the ring of distinct input frame sets, resident in HBM
+    frames = [synth.frame_set(wl, t, device=dev) for t in range(ring)]
+    crops = [synth.crop_list(wl, t) for t in range(ring)] if wl.n_crops else None
+    torch.cuda.synchronize()
+    arr = rt.CameraArray(wl.cams, stream=stream, **array_kwargs(args, wl))
+    t_sub = [0]
+
+    def submit_one():
+        i = t_sub[0] % ring
+        arr.submit_frames(frames[i], t_sub[0], crops[i] if crops else ())
+        t_sub[0] += 1
+
+    def ring_order(n):
+        order = [(t_sub[0] + j) % ring for j in range(n)]
+        return [frames[i] for i in order], ([crops[i] for i in order] if crops else None)
+
+    # warm-up: W frame sets (the first starts the sequence)
+    for _ in range(max(1, W)):
+        submit_one()
+    arr.sync()
+    # launch shapes: timed on this ring (untimed here), cached per device and array
+    tuning = None
+    if autotune:
+        fr, cr = ring_order(ring)
+        cache = os.path.join(tempfile.gettempdir(), "rt_tuning_%d.json" % os.getpid())
+        tuning = arr.autotune(fr, cr, cache_path=cache)
+        try:
+            os.remove(cache)
+        except OSError:
+            pass
+        arr.sync()
+    # the timed graph, captured at the ring position where the timed region starts
+    L, launches, singles = graph_plan(K)
+    if timing_events != "none":
+        arr.profile(True, pass_b_only=timing_events == "pass_b")
+    arr.capture_sequence(*ring_order(L))
+    arr.profile(False)
+    arr.sync()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev.index)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(launches):
+        arr.launch_sequence()
+        t_sub[0] += L
+    for _ in range(singles):
+        submit_one()
+    arr.stream_wait(stream)
+    e1.record(stream)
+    e1.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = arr.get_profile()     # pass B launches of the timed region's last graph launch
+    # the same graph once more, after single submits restore its slot
+    # alignment: shows whether its first launch cost more than a relaunch
+    relaunch_ms = None
+    if launches == 1 and singles == 0:
+        for _ in range((6 - L % 6) % 6):
+            submit_one()
+        arr.sync()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        arr.launch_sequence()
+        t_sub[0] += L
+        arr.stream_wait(stream)
+        r1.record(stream)
+        r1.synchronize()
+        relaunch_ms = r0.elapsed_time(r1) / L
+    # per-pass breakdown: a ring captured with events around every pass,
+    # launched outside the timed region
+    arr.sync()
+    arr.profile(True)
+    arr.capture_sequence(*ring_order(ring))
+    arr.profile(False)
+    for _ in range(3):
+        arr.launch_sequence()
+        t_sub[0] += ring
+    prof_all = arr.get_profile()
+    arr.profile(False)
+    arr.close()
+    n_all = max(1, prof_all["frame_sets"])
+    pass_ms = {k: prof_all[k + "_ms"] / n_all for k in ("pass_a", "solve", "pass_b", "crops")}
+    pb_ms = prof["pass_b_ms"] / max(1, prof["frame_sets"]) if prof["frame_sets"] else pass_ms["pass_b"]
+    del frames
+    return {"ms": ms, "K": K, "W": W, "ring": ring, "ring_bytes": ring * in_bytes, "l2": l2,
+            "plan": {"graph_frame_sets": L, "graph_launches": launches, "single_submits": singles},
+            "relaunch_ms_per_set": relaunch_ms, "clocks": ck, "tuning": tuning,
+            "pb_ms": pb_ms, "pb_timed_sets": prof["frame_sets"], "pass_ms": pass_ms,
+            "crops": crops}
+
+
+def roofline_pass_b(wl, pb_ms, peak, peak_kind, traffic):
+    ab = alg_bytes(wl)
+    achieved = ab / (pb_ms / 1e3) / 1e9 if pb_ms > 0 else None
+    return {"bound": "hbm", "kernel": "pass_b (convert + frame histograms + Q16 apply)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+            "traffic": traffic, "alg_bytes_per_launch": ab}
+
+
+def workload_line(args, wl, m, peak, peak_kind, world=1):
+    """Summary of one measured workload (the extra configurations)."""
+    px = wl.pixels
+    K = m["K"]
+    d = {"config": config_dict(args, wl, "ring of %d distinct input frame sets (%.0f MB) > 4x L2" %
+                               (m["ring"], m["ring_bytes"] / 1e6)),
+         "value": world * K * px / (m["ms"] / 1e3) / 1e6, "unit": "Mpix/s", "steps": K, "warmup": m["W"],
+         "ms_per_step": m["ms"] / K, "array_fps": world * K / (m["ms"] / 1e3),
+         "hbm_frac_whole_step": K * alg_bytes(wl) / (m["ms"] / 1e3) / 1e9 / peak,
+         "graph_plan": m["plan"], "relaunch_ms_per_step": m["relaunch_ms_per_set"],
+         "roofline_pass_b": roofline_pass_b(wl, m["pb_ms"], peak, peak_kind, None),
+         "pass_ms_per_set": m["pass_ms"], "clocks": m["clocks"], "tuning": m["tuning"]}
+    if wl.n_crops and m["crops"]:
+        import numpy as np
+        cb = float(np.mean([crop_alg_bytes(c, wl.crop_out) for c in m["crops"]]))
+        cms = m["pass_ms"]["crops"]
+        ach = cb / (cms / 1e3) / 1e9 if cms > 0 else None
+        d["roofline_crops"] = {"bound": "hbm", "kernel": "crops_cols_kernel (bilinear -> FP16 NCHW)",
+                               "achieved": ach, "peak": peak, "unit": "GB/s",
+                               "frac": ach / peak if ach else None, "peak_kind": peak_kind, "traffic": None,
+                               "alg_bytes_per_launch": cb,
+                               "timing": "all-pass events, graph launched outside the timed region"}
+    return d
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -525,105 +737,36 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     wl = workload(args.workload)
     K, W = args.steps, args.warmup
-    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
-    in_bytes = input_bytes(wl)
-    ring = args.ring or max(6, -(-int(4 * l2 / in_bytes + 1) // 6) * 6)
-    ring = max(6, ring - ring % 6)
-    # the ring of distinct input frame sets, resident in HBM
-    frames = [synth.frame_set(wl, t, device=dev) for t in range(ring)]
-    crops = [synth.crop_list(wl, t) for t in range(ring)] if wl.n_crops else None
-    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    arr = rt.CameraArray(wl.cams, stream=stream, **array_kwargs(args, wl))
-
-    t_sub = [0]
-
-    def submit_one():
-        i = t_sub[0] % ring
-        arr.submit_frames(frames[i], t_sub[0], crops[i] if crops else ())
-        t_sub[0] += 1
-
-    # Warm-up: W frame sets.  Frame set 0 starts the sequence; the graph over
-    # the ring is captured (with profiling events inside) at the ring position
-    # where the timed region will start, and launched once in the warm-up when
-    # W leaves room for a whole ring.
-    warm_graph = W - 1 >= ring
-    singles = (W - 1 - ring) if warm_graph else (W - 1)
-    for _ in range(1 + max(0, singles)):
-        submit_one()
-    arr.sync()
-    # launch shapes: timed on this ring (untimed here), cached per device and array
-    tuning = None
-    if not args.no_autotune:
-        order = [(t_sub[0] + j) % ring for j in range(ring)]
-        cache = os.path.join(tempfile.gettempdir(), "rt_tuning_%d.json" % os.getpid())
-        tuning = arr.autotune([frames[i] for i in order], [crops[i] for i in order] if crops else None,
-                              cache_path=cache)
-        try:
-            os.remove(cache)
-        except OSError:
-            pass
-        arr.sync()
-    if args.timing_events != "none":
-        arr.profile(True, pass_b_only=args.timing_events == "pass_b")
-    order = [(t_sub[0] + j) % ring for j in range(ring)]
-    arr.capture_sequence([frames[i] for i in order], [crops[i] for i in order] if crops else None)
-    arr.profile(False)
-    if warm_graph:
-        arr.launch_sequence()
-        t_sub[0] += ring
-    arr.sync()
+    in_bytes = input_bytes(wl)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    clocks = Clocks(local)
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(K // ring):
-        arr.launch_sequence()
-        t_sub[0] += ring
-    for _ in range(K % ring):
-        submit_one()
-    arr.stream_wait(stream)
-    e1.record(stream)
-    e1.synchronize()
-    ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    m = measure(args, wl, K, W, dev, stream, autotune=not args.no_autotune, timing_events=args.timing_events)
+    ms = m["ms"]
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-        if world > 1:
-            dist.barrier()
-    prof = arr.get_profile()     # pass B launches of the timed region's last graph launch
-    # per-pass breakdown: the same ring captured again with events around
-    # every pass, launched outside the timed region
-    arr.profile(True)
-    order = [(t_sub[0] + j) % ring for j in range(ring)]
-    arr.capture_sequence([frames[i] for i in order], [crops[i] for i in order] if crops else None)
-    arr.profile(False)
-    for _ in range(3):
-        arr.launch_sequence()
-        t_sub[0] += ring
-    prof_all = arr.get_profile()
-    arr.profile(False)
+        dist.barrier()
     px_set = wl.pixels
     value = world * K * px_set / (ms / 1e3) / 1e6
-    # roofline of the dominant kernel, pass B
     peak, peak_kind = measured_peak()
-    pb_ms = prof["pass_b_ms"] / max(1, prof["frame_sets"])
     ab = alg_bytes(wl)
-    achieved = ab / (pb_ms / 1e3) / 1e9 if pb_ms > 0 else None
-    traffic = ncu_traffic(args.workload)
+    roof = roofline_pass_b(wl, m["pb_ms"], peak, peak_kind, ncu_traffic(args.workload))
+    roof["timed_frame_sets"] = m["pb_timed_sets"]
+    roof["pass_ms_per_set"] = m["pass_ms"]
     launches_per_set = 3 + (1 if wl.n_crops else 0) + (2 if args.attention else 0) + (1 if args.seam_cost else 0)
+    tuning = m["tuning"]
 
     # end to end through the host-buffer entry point
     e2e = None
     ke = max(6, min(args.e2e_steps, K))
     if rank == 0 or world > 1:
+        ring = m["ring"]
+        crops = m["crops"]
         nh = 3
-        host = [[{k: v.cpu().pin_memory() for k, v in f.items()} for f in frames[i]] for i in range(nh)]
+        host = [[{k: v.cpu().pin_memory() for k, v in f.items()} for f in synth.frame_set(wl, i, device=dev)]
+                for i in range(nh)]
         opitch = 3 * max(c.width for c in wl.cams)
         outs = [[torch.empty((c.height, opitch), dtype=torch.uint8).pin_memory() for c in wl.cams]
                 for _ in range(2)]
@@ -647,11 +790,33 @@ def run_ours(args):
         s1.record(stream)
         s1.synchronize()
         ems = s0.elapsed_time(s1)
+        arr2.close()
+        del host, outs
         h2d = in_bytes
         d2h = sum(3 * c.width * c.height for c in wl.cams)
+        link = host_link_peaks(dev)
+        per_set = ems / 1e3 / ke
+        bound = max(h2d / (link["h2d"] * 1e9), d2h / (link["d2h"] * 1e9), (h2d + d2h) / (link["both"] * 1e9))
         e2e = {"value": world * ke * px_set / (ems / 1e3) / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": ke}
-        arr2.close()
+               "d2h_bytes_per_step": d2h, "steps": ke,
+               "roofline": {"bound": "host link", "achieved_gbs": (h2d + d2h) / per_set / 1e9,
+                            "link_gbs": {k: link[k] for k in ("h2d", "d2h", "both")},
+                            "bound_us_per_step": bound * 1e6, "us_per_step": per_set * 1e6,
+                            "frac": bound / per_set,
+                            "note": "link peaks: pinned cudaMemcpyAsync of %d MB, each direction alone and "
+                                    "both at once, measured in this run; bound = max(in/h2d, out/d2h, "
+                                    "(in+out)/both)" % (link["bytes_per_copy"] >> 20)}}
+
+    # the other array configurations, each with its own roofline (rank 0 only)
+    extras = None
+    if rank == 0 and not args.no_extras and args.workload == "tower12":
+        extras = {}
+        for name, ke_x in (("uneven", 120), ("stress", 60)):
+            wlx = workload(name)
+            mx = measure(args, wlx, ke_x, 6, dev, stream, autotune=not args.no_autotune)
+            extras[wlx.name] = workload_line(args, wlx, mx, peak, peak_kind)
+            del mx
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -665,14 +830,13 @@ def run_ours(args):
         except Exception as exc:   # the single-thread figure is context only
             cpu["single_thread"] = {"error": repr(exc)}
 
-    arr.close()
     sur = None
     if rank == 0 and not args.no_surrogate:
         sur = surrogate_report(args)
     trk = track_report() if rank == 0 and not args.no_track else None
     if rank == 0:
         ring_desc = "ring of %d distinct input frame sets (%.0f MB) > 4x L2 (%.0f MB); outputs double buffered" % (
-            ring, ring * in_bytes / 1e6, l2 / 1e6)
+            m["ring"], m["ring_bytes"] / 1e6, m["l2"] / 1e6)
         line = {
             "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
@@ -680,21 +844,14 @@ def run_ours(args):
             "config": config_dict(args, wl, ring_desc),
             "array_fps": world * K / (ms / 1e3),
             "hbm_frac_whole_step": (world * K * ab / (ms / 1e3) / 1e9) / peak / world,
-            "roofline": {"bound": "hbm", "kernel": "pass_b (convert + frame histograms + Q16 apply)",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                         "traffic": traffic, "alg_bytes_per_launch": ab,
-                         "timed_frame_sets": prof["frame_sets"],
-                         # all passes evented, outside the timed region (events cost time)
-                         "pass_ms_per_set": {"pass_a": prof_all["pass_a_ms"] / max(1, prof_all["frame_sets"]),
-                                             "solve": prof_all["solve_ms"] / max(1, prof_all["frame_sets"]),
-                                             "pass_b": prof_all["pass_b_ms"] / max(1, prof_all["frame_sets"]),
-                                             "crops": prof_all["crops_ms"] / max(1, prof_all["frame_sets"])}},
+            "graph_plan": m["plan"], "relaunch_ms_per_step": m["relaunch_ms_per_set"],
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": K * launches_per_set,
-            "clocks": ck,
+            "clocks": m["clocks"],
             "tuning": tuning,
+            "extra_workloads": extras,
             "surrogate": sur,
             "detections": trk,
         }

@@ -290,17 +290,21 @@ rt_status rt_stream_wait(rt_handle *h, void *cuda_stream);
  * ring of input buffers (a decoder's surface pool): set i uses
  * y_planes[i*K + k] / uv_planes[i*K + k] (device pointers, as for
  * rt_submit_frames) and crops[i*max_crops .. + n_crops[i]) (crops and
- * n_crops may be NULL for none).  n_sets must be a positive multiple of 6.
- * At least one frame set must have been submitted before (the graph
- * continues a sequence; it never restarts one).  The graph's parameters are
- * fixed at capture; the buffers must stay allocated while it exists.  A new
- * capture replaces the previous one. */
+ * n_crops may be NULL for none).  n_sets >= 1.  The graph's buffer slots
+ * repeat every 6 frame sets, so it can be launched whenever the frame sets
+ * submitted since the capture are a multiple of 6: a graph of a multiple of 6
+ * frame sets runs back to back; one of another length runs once, or again
+ * after single submits restore the alignment.  At least one frame set must
+ * have been submitted before (the graph continues a sequence; it never
+ * restarts one).  The graph's parameters are fixed at capture; the buffers
+ * must stay allocated while it exists.  A new capture replaces the previous
+ * one. */
 rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y_planes,
                               const void *const *uv_planes, const rt_crop *crops, const int32_t *n_crops);
 
 /* Launch the captured graph once: n_sets more frame sets of the sequence,
- * one graph launch.  RT_ERR_STATE if nothing is captured or if frame sets
- * submitted in between broke the ring's slot alignment (a multiple of 6). */
+ * one graph launch.  RT_ERR_STATE if nothing is captured or if the frame
+ * sets submitted since the capture are not a multiple of 6. */
 rt_status rt_launch_sequence(rt_handle *h);
 
 /* Launch shapes of the per-frame-set kernels.  Throughput depends on them

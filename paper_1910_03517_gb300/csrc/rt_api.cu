@@ -1145,7 +1145,7 @@ rt_status rt_capture_sequence(rt_handle *h, int32_t n_sets, const void *const *y
 {
     if (!h) return RT_ERR_INVALID;
     const int K = h->p.num_cameras, M = h->p.max_crops;
-    if (n_sets <= 0 || n_sets % 6) return fail(h, RT_ERR_INVALID, "n_sets must be a positive multiple of 6");
+    if (n_sets <= 0) return fail(h, RT_ERR_INVALID, "n_sets must be positive");
     if (h->t == 0) return fail(h, RT_ERR_STATE, "submit the first frame set of the sequence before capturing");
     if (!y_planes) return fail(h, RT_ERR_INVALID, "y_planes is NULL");
     rt_status s;
@@ -1235,6 +1235,8 @@ rt_status rt_launch_sequence(rt_handle *h)
 {
     if (!h) return RT_ERR_INVALID;
     if (!h->graph_exec) return fail(h, RT_ERR_STATE, "no captured sequence");
+    // the graph's buffer slots are fixed at capture: output parity (period 2)
+    // and the statistics / Q16 rings (period 3)
     if ((h->t - h->cap_t0) % 6 != 0) return fail(h, RT_ERR_STATE, "frame sets submitted since the capture broke its slot alignment");
     RT_CUDA(h, cudaEventRecord(h->ev_user, h->user));
     RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_user, 0));

@@ -414,7 +414,8 @@ class CameraArray:
         return n, y, uv, cr_p, nc_p
 
     def capture_sequence(self, frame_sets, crops_per_set=None):
-        """Capture a graph over a fixed ring of frame sets (len a multiple of 6)."""
+        """Capture a graph over these frame sets (any number; relaunchable while
+        the frame sets submitted since the capture are a multiple of 6)."""
         n, y, uv, cr_p, nc_p = self._sequence_args(frame_sets, crops_per_set)
         st = self.L.rt_capture_sequence(self.h, n, y, uv, cr_p, nc_p)
         _check(self.L, self.h, st)
