@@ -31,6 +31,20 @@ extern "C" {
 rt_status rt_check_solve_math(int32_t n, const uint64_t *a, const uint64_t *b, double *log_ratio, const double *x,
                               double *exp_x);
 
+/* Intermediate values of the learned surrogate's last rt_mlp_gradients call
+ * (rt_surrogate.h), so that tests can run the FP64 oracle's layer steps on the
+ * GPU's own operands (identical BF16 activations and ReLU masks) layer by
+ * layer.  Host buffers (any may be NULL), for the call's n batch rows:
+ *   h1, h2   BF16 bits [n][256]: relu(x W1^T + b1) and relu(h1 W2^T + b2);
+ *   dz2      BF16 bits [n][256]: (dL/dy W3) masked by h2 > 0;
+ *   dz1t     BF16 bits [256][256]: (dz2 W2) masked by h1 > 0, TRANSPOSED
+ *            (column b = batch row b; columns >= n are zero);
+ *   y        FP32 [n][3]: the network's outputs.
+ * Waits for the network's stream.  RT_ERR_INVALID for n outside 1..256. */
+typedef struct rt_mlp rt_mlp;
+rt_status rt_mlp_check_activations(rt_mlp *m, int32_t n, uint16_t *h1, uint16_t *h2, uint16_t *dz2,
+                                   uint16_t *dz1t, float *y);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,14 +58,50 @@ def _add(z, bias, acc32):
     return (z.astype(np.float32) + np.asarray(bias, np.float32)).astype(np.float64) if acc32 else z + bias
 
 
+def _rounder(bf16: bool):
+    return bf16_round if bf16 else (lambda a: np.asarray(a, np.float64))
+
+
+def dense_relu(h: np.ndarray, W: np.ndarray, b: np.ndarray, bf16: bool = True, acc32: bool = False):
+    """One hidden layer: pre-activation z = h W^T + b and the stored
+    activation relu(z) (rounded to BF16 when ``bf16``).  W as used (already
+    BF16-rounded when the network stores BF16 weights)."""
+    z = _add(_mm(h, np.asarray(W).T, acc32), b, acc32)
+    return z, _rounder(bf16)(np.maximum(z, 0.0))
+
+
+def output_layer(h2: np.ndarray, W3: np.ndarray, b3: np.ndarray, acc32: bool = False) -> np.ndarray:
+    """The linear output layer y = h2 W3^T + b3 (three log-gains per row)."""
+    return _add(_mm(h2, np.asarray(W3).T, acc32), b3, acc32)
+
+
+def output_grad(y: np.ndarray, t: np.ndarray, acc32: bool = False) -> np.ndarray:
+    """dL/dy of L = mean over the batch and the three outputs of (y - t)^2."""
+    N = t.shape[0]
+    if acc32:
+        return (np.float32(2.0) * (np.asarray(y, np.float32) - np.asarray(t, np.float32)) /
+                np.float32(N * D_OUT)).astype(np.float64)
+    return 2.0 * (y - t) / (N * D_OUT)
+
+
+def hidden_grad(dz_next: np.ndarray, W_next: np.ndarray, active: np.ndarray, bf16: bool = True,
+                acc32: bool = False) -> np.ndarray:
+    """dL/dz of a hidden layer from the next layer's dL/dz and weights (as
+    used): (dz_next W_next) where the ReLU was active, else 0 (stored BF16)."""
+    return _rounder(bf16)(_mm(dz_next, W_next, acc32) * active)
+
+
+def weight_grads(dz: np.ndarray, h_in: np.ndarray):
+    """dL/dW = dz^T h_in and dL/db = sum of dz over the batch (FP64)."""
+    return dz.T @ h_in, dz.sum(0)
+
+
 def forward(P: Dict[str, np.ndarray], X: np.ndarray, bf16: bool = True, acc32: bool = False):
-    r = bf16_round if bf16 else (lambda a: np.asarray(a, np.float64))
+    r = _rounder(bf16)
     x = r(X)
-    z1 = _add(_mm(x, r(P["W1"]).T, acc32), P["b1"], acc32)
-    h1 = r(np.maximum(z1, 0.0))
-    z2 = _add(_mm(h1, r(P["W2"]).T, acc32), P["b2"], acc32)
-    h2 = r(np.maximum(z2, 0.0))
-    y = _add(_mm(h2, r(P["W3"]).T, acc32), P["b3"], acc32)
+    z1, h1 = dense_relu(x, r(P["W1"]), P["b1"], bf16, acc32)
+    z2, h2 = dense_relu(h1, r(P["W2"]), P["b2"], bf16, acc32)
+    y = output_layer(h2, r(P["W3"]), P["b3"], acc32)
     return y, {"x": x, "z1": z1, "h1": h1, "z2": z2, "h2": h2, "y": y}
 
 
@@ -75,19 +111,14 @@ def mse(y: np.ndarray, t: np.ndarray) -> float:
 
 def backward(P: Dict[str, np.ndarray], cache, t: np.ndarray, bf16: bool = True, acc32: bool = False):
     """Gradients of mean((y - t)^2) over the batch and the three outputs."""
-    r = bf16_round if bf16 else (lambda a: np.asarray(a, np.float64))
-    N = t.shape[0]
-    dy = 2.0 * (cache["y"] - t) / (N * D_OUT)
-    if acc32:
-        dy = (np.float32(2.0) * (cache["y"].astype(np.float32) - np.asarray(t, np.float32)) /
-              np.float32(N * D_OUT)).astype(np.float64)
-    g = {"W3": dy.T @ cache["h2"], "b3": dy.sum(0)}
-    dh2 = r(_mm(dy, r(P["W3"]), acc32) * (cache["z2"] > 0))
-    g["W2"] = dh2.T @ cache["h1"]
-    g["b2"] = dh2.sum(0)
-    dh1 = r(_mm(dh2, r(P["W2"]), acc32) * (cache["z1"] > 0))
-    g["W1"] = dh1.T @ cache["x"]
-    g["b1"] = dh1.sum(0)
+    r = _rounder(bf16)
+    dy = output_grad(cache["y"], t, acc32)
+    g = {}
+    g["W3"], g["b3"] = weight_grads(dy, cache["h2"])
+    dh2 = hidden_grad(dy, r(P["W3"]), cache["z2"] > 0, bf16, acc32)
+    g["W2"], g["b2"] = weight_grads(dh2, cache["h1"])
+    dh1 = hidden_grad(dh2, r(P["W2"]), cache["z1"] > 0, bf16, acc32)
+    g["W1"], g["b1"] = weight_grads(dh1, cache["x"])
     return g
 
 

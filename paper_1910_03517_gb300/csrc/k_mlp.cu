@@ -21,6 +21,7 @@
 #include "rt_internal.cuh"
 #include "tc_gemm.cuh"
 #include "../../include/rt_surrogate.h"
+#include "../../include/rt_check.h"
 
 using namespace rt;
 
@@ -497,6 +498,21 @@ rt_status rt_mlp_train_step(rt_mlp *m, const void *x_bf16, const float *t, int32
 }
 
 const char *rt_mlp_last_error(rt_mlp *m) { return m ? m->msg.c_str() : ""; }
+
+rt_status rt_mlp_check_activations(rt_mlp *m, int32_t n, uint16_t *h1, uint16_t *h2, uint16_t *dz2,
+                                   uint16_t *dz1t, float *y)
+{
+    if (!m) return RT_ERR_INVALID;
+    if (n < 1 || n > MAXB) return mfail(m, RT_ERR_INVALID, "n must be in 1..256");
+    const size_t row = (size_t)D_H * 2;
+    if (h1) MC(m, cudaMemcpyAsync(h1, m->H1, (size_t)n * row, cudaMemcpyDeviceToHost, m->s));
+    if (h2) MC(m, cudaMemcpyAsync(h2, m->H2, (size_t)n * row, cudaMemcpyDeviceToHost, m->s));
+    if (dz2) MC(m, cudaMemcpyAsync(dz2, m->dZ2, (size_t)n * row, cudaMemcpyDeviceToHost, m->s));
+    if (dz1t) MC(m, cudaMemcpyAsync(dz1t, m->dZ1T, (size_t)D_H * MAXB * 2, cudaMemcpyDeviceToHost, m->s));
+    if (y) MC(m, cudaMemcpyAsync(y, m->Y, (size_t)n * D_OUT * 4, cudaMemcpyDeviceToHost, m->s));
+    MC(m, cudaStreamSynchronize(m->s));
+    return RT_OK;
+}
 
 }  // extern "C"
 

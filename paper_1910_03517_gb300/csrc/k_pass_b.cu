@@ -60,6 +60,67 @@ __device__ __forceinline__ void magic2(float z0, float z1, uint32_t &b0, uint32_
         : "=r"(b0), "=r"(b1) : "f"(z0), "f"(z1), "f"(255.0f), "f"(kMagic));
 }
 
+// Two values' float arithmetic in one packed FP32x2 instruction (the same
+// round-to-nearest IEEE result per lane as the scalar instruction).
+struct F2 { float x, y; };
+
+__device__ __forceinline__ F2 fma2(F2 a, float k, F2 c)
+{
+    F2 d;
+    asm("{\n .reg .b64 a, k, c, r;\n"
+        " mov.b64 a, {%2, %3};\n"
+        " mov.b64 k, {%4, %4};\n"
+        " mov.b64 c, {%5, %6};\n"
+        " fma.rn.f32x2 r, a, k, c;\n"
+        " mov.b64 {%0, %1}, r;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(k), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+__device__ __forceinline__ F2 fma2(F2 a, float k, float c)
+{
+    F2 d;
+    asm("{\n .reg .b64 a, k, c, r;\n"
+        " mov.b64 a, {%2, %3};\n"
+        " mov.b64 k, {%4, %4};\n"
+        " mov.b64 c, {%5, %5};\n"
+        " fma.rn.f32x2 r, a, k, c;\n"
+        " mov.b64 {%0, %1}, r;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(k), "f"(c));
+    return d;
+}
+
+// Bytes i and j of w as floats (0..255): two PRMTs and one packed FADD that
+// removes the 2^23 of the bit trick from both.
+__device__ __forceinline__ F2 bytes_f2(uint32_t w, int i, int j)
+{
+    const uint32_t bi = __byte_perm(w, kMagicBits, 0x7440u | (uint32_t)i);
+    const uint32_t bj = __byte_perm(w, kMagicBits, 0x7440u | (uint32_t)j);
+    F2 d;
+    asm("{\n .reg .b64 a, m, r;\n"
+        " mov.b64 a, {%2, %3};\n"
+        " mov.b64 m, {%4, %4};\n"
+        " add.rn.f32x2 r, a, m;\n"
+        " mov.b64 {%0, %1}, r;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "r"(bi), "r"(bj), "f"(-kMagic));
+    return d;
+}
+
+// Clamped output bytes of two applied values: t = 65536 v' + low bits, the
+// result min(v', 255) (v' < 2^16).  Returns [min(t0>>16, 255), 0,
+// min(t1>>16, 255), 0] -- one PRMT gathers the high halves, one packed
+// 16-bit min clamps both.
+__device__ __forceinline__ uint32_t clamp_hi2(uint32_t t0, uint32_t t1)
+{
+    const uint32_t hi = __byte_perm(t0, t1, 0x7632u);
+    uint32_t r;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(hi), "r"(0x00FF00FFu));
+    return r;
+}
+
+// Bytes 0 and 2 of a and of b: [a.0, a.2, b.0, b.2].
+__device__ __forceinline__ uint32_t even_bytes(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x6420u); }
+
 // Pack byte 2 of four values into one word (t0 lowest): three PRMTs.
 __device__ __forceinline__ uint32_t pack4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3)
 {
@@ -249,29 +310,29 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
 
 #pragma unroll
     for (int g4 = 0; g4 < 4; ++g4) {                  // pixels 4 g4 .. 4 g4 + 3
-        float cz[2][3];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {                 // chroma pairs 2 g4, 2 g4 + 1
-            const float Uf = byte_f(uvw[g4], 2 * h);
-            const float Vf = byte_f(uvw[g4], 2 * h + 1);
-            cz[h][0] = fmaf(Vf, k.krv, k.c_r0);
-            cz[h][1] = fmaf(Uf, k.kgu, fmaf(Vf, k.kgv, k.c_g0));
-            cz[h][2] = fmaf(Uf, k.kbu, k.c_b0);
-        }
+        // chroma pairs 2 g4, 2 g4 + 1: (U, V) bytes 0, 1 and 2, 3 of the word,
+        // both pairs' chroma terms at once in packed FP32x2
+        const F2 Uf = bytes_f2(uvw[g4], 0, 2), Vf = bytes_f2(uvw[g4], 1, 3);
+        const F2 czR = fma2(Vf, k.krv, k.c_r0);
+        const F2 czG = fma2(Uf, k.kgu, fma2(Vf, k.kgv, k.c_g0));
+        const F2 czB = fma2(Uf, k.kbu, k.c_b0);
+        const float cz[2][3] = {{czR.x, czG.x, czB.x}, {czR.y, czG.y, czB.y}};
         if constexpr (FIT == RT_FIT_GLOBAL) {
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 uint32_t t[12];
-                // conversion of the 4 pixels: 12 saturated z, rounded two at a time
+                // conversion of the 4 pixels: luma pairs as packed floats,
+                // 12 saturated z, rounded two at a time
                 uint32_t vbq[4][3];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {             // pixels 2h, 2h+1 share a chroma pair
-                    const float Y0f = byte_f(yw[r][g4], 2 * h), Y1f = byte_f(yw[r][g4], 2 * h + 1);
+                    const F2 Yf = bytes_f2(yw[r][g4], 2 * h, 2 * h + 1);
+                    const float czh[3] = {h ? czR.y : czR.x, h ? czG.y : czG.x, h ? czB.y : czB.x};
                     float z0[3], z1[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        z0[c] = __saturatef(fmaf(Y0f, k.ky, cz[h][c]));
-                        z1[c] = __saturatef(fmaf(Y1f, k.ky, cz[h][c]));
+                        z0[c] = __saturatef(fmaf(Yf.x, k.ky, czh[c]));
+                        z1[c] = __saturatef(fmaf(Yf.y, k.ky, czh[c]));
                     }
                     magic2(z0[0], z0[1], vbq[2 * h][0], vbq[2 * h][1]);
                     magic2(z1[0], z1[1], vbq[2 * h + 1][0], vbq[2 * h + 1][1]);
@@ -286,14 +347,13 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
                         if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vb[c];
                         const bool live = FULL || i < nvalid;
                         if (STATS && live) red_shared_inc(hbase + vb[c] * 128u + (uint32_t)c * 32768u);
-                        uint32_t tt = rg[r].aq[c] * vb[c] + rg[r].cq[c];
-                        tt = tt > 0xFFFFFFu ? 0xFFFFFFu : tt;
-                        t[3 * q + c] = tt;
+                        t[3 * q + c] = rg[r].aq[c] * vb[c] + rg[r].cq[c];   // 65536 out + low bits, unclamped
                     }
                 }
-                ow[r][3 * g4 + 0] = pack4(t[0], t[1], t[2], t[3]);
-                ow[r][3 * g4 + 1] = pack4(t[4], t[5], t[6], t[7]);
-                ow[r][3 * g4 + 2] = pack4(t[8], t[9], t[10], t[11]);
+                // clamp to 255 and pack: [R0 G0 B0 R1] [G1 B1 R2 G2] [B2 R3 G3 B3]
+                ow[r][3 * g4 + 0] = even_bytes(clamp_hi2(t[0], t[1]), clamp_hi2(t[2], t[3]));
+                ow[r][3 * g4 + 1] = even_bytes(clamp_hi2(t[4], t[5]), clamp_hi2(t[6], t[7]));
+                ow[r][3 * g4 + 2] = even_bytes(clamp_hi2(t[8], t[9]), clamp_hi2(t[10], t[11]));
             }
         } else {
             // conversion of the 4 pixels of both rows: 12 saturated z per row,

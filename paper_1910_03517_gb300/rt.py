@@ -542,6 +542,7 @@ def _load_mlp(L):
     L.rt_mlp_last_error.restype = ctypes.c_char_p
     L.rt_mlp_destroy.argtypes = [c_vp]
     L.rt_mlp_destroy.restype = None
+    L.rt_mlp_check_activations.argtypes = [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]
     L.rt_surrogate_predict.argtypes = [c_vp, c_vp, c_vp, c_vp, c_i32]
     L.rt_surrogate_predict.restype = c_i32
     for n in MLP_EXPORTS[:-3]:
@@ -602,6 +603,18 @@ class GainMLP:
         loss = np.zeros(1, np.float32)
         self._chk(self.L.rt_mlp_gradients(self.h, x.data_ptr(), t.data_ptr(), n, g.ctypes.data, loss.ctypes.data))
         return g, float(loss[0])
+
+    def activations(self, n: int) -> Dict[str, np.ndarray]:
+        """The last gradients() call's intermediate values (rt_check.h), BF16
+        as float64: h1, h2, dz2 [n, 256]; dz1 [n, 256]; y [n, 3] (FP32)."""
+        u = lambda shape: np.zeros(shape, np.uint16)
+        h1, h2, dz2, dz1t = u((n, 256)), u((n, 256)), u((n, 256)), u((256, 256))
+        y = np.zeros((n, 3), np.float32)
+        self._chk(self.L.rt_mlp_check_activations(self.h, n, h1.ctypes.data, h2.ctypes.data, dz2.ctypes.data,
+                                                  dz1t.ctypes.data, y.ctypes.data))
+        f = lambda a: (a.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        return {"h1": f(h1), "h2": f(h2), "dz2": f(dz2), "dz1": f(np.ascontiguousarray(dz1t[:, :n].T)),
+                "y": y.astype(np.float64)}
 
     def train_step(self, x, t, lr: float) -> float:
         loss = np.zeros(1, np.float32)
