@@ -44,6 +44,21 @@ __device__ __forceinline__ void red_shared_inc(uint32_t addr)
     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
 }
 
+// Histogram increment of channel C: the channel's 32 KB offset rides in the
+// instruction's immediate address field.
+template <int C>
+__device__ __forceinline__ void red_shared_inc_c(uint32_t addr)
+{
+    asm volatile("red.shared.add.u32 [%0+%1], 1;" ::"r"(addr), "n"(C * 32768) : "memory");
+}
+
+__device__ __forceinline__ void hist_inc(uint32_t addr, int c)
+{
+    if (c == 0) red_shared_inc_c<0>(addr);
+    else if (c == 1) red_shared_inc_c<1>(addr);
+    else red_shared_inc_c<2>(addr);
+}
+
 // Apply constants of one row for the per-camera gain fit: t = a_q * vbits + cq
 struct RowGain { uint32_t aq[3], cq[3]; };
 
@@ -279,7 +294,7 @@ template <int FIT, bool STATS, bool FULL, bool THUMBS>
 __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, int ux, const ConvConsts &k,
                                           const int32_t *__restrict__ q16, int B, uint32_t hbase, uint32_t *th,
                                           bool seg, uint32_t sa0, uint32_t sa1, uint32_t sa2,
-                                          const uint4 Y0, const uint4 Y1, const uint4 UV)
+                                          const uint4 Y0, const uint4 Y1, const uint4 UV, uint32_t (&ow)[2][12])
 {
     const int x0 = ux * kUnitCols;
     const int y0 = rp * 2;
@@ -305,7 +320,6 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
         jr[0] = block_of_row(y0, cg.H, cg.nblk);
         jr[1] = block_of_row(y0 + 1, cg.H, cg.nblk);
     }
-    uint32_t ow[2][12];
     uint32_t tv[THUMBS ? 2 : 1][THUMBS ? kUnitCols : 1][3];
 
 #pragma unroll
@@ -346,7 +360,7 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
                     for (int c = 0; c < 3; ++c) {
                         if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vb[c];
                         const bool live = FULL || i < nvalid;
-                        if (STATS && live) red_shared_inc(hbase + vb[c] * 128u + (uint32_t)c * 32768u);
+                        if (STATS && live) hist_inc(hbase + vb[c] * 128u, c);
                         t[3 * q + c] = rg[r].aq[c] * vb[c] + rg[r].cq[c];   // 65536 out + low bits, unclamped
                     }
                 }
@@ -383,7 +397,7 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vbq[r][q][c];
-                        if (STATS && live) red_shared_inc(hbase + vbq[r][q][c] * 128u + (uint32_t)c * 32768u);
+                        if (STATS && live) hist_inc(hbase + vbq[r][q][c] * 128u, c);
                     }
                 }
             uint32_t t[2][12];
@@ -424,15 +438,11 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
         thumb_row<FULL>(th, cg, y0, x0, nvalid, tv[0]);
         thumb_row<FULL>(th, cg, y0 + 1, x0, nvalid, tv[1]);
     }
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        uint8_t *dst = cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0;
-        if (FULL) {
-            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-            d4[0] = make_uint4(ow[r][0], ow[r][1], ow[r][2], ow[r][3]);
-            d4[1] = make_uint4(ow[r][4], ow[r][5], ow[r][6], ow[r][7]);
-            d4[2] = make_uint4(ow[r][8], ow[r][9], ow[r][10], ow[r][11]);
-        } else {
+    // a full unit's 48 bytes per row go out through store_unit; a ragged one
+    // writes its bytes here
+    if (!FULL) {
+        for (int r = 0; r < 2; ++r) {
+            uint8_t *dst = cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0;
             for (int b = 0; b < 3 * nvalid; ++b) dst[b] = (uint8_t)(ow[r][b >> 2] >> (8 * (b & 3)));
         }
     }
@@ -440,12 +450,12 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
 
 template <int FIT, bool STATS, bool FULL, bool THUMBS>
 __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, int ux,
-                                          const int32_t *__restrict__ q16, int B, uint32_t hbase, uint32_t *th)
+                                          const int32_t *__restrict__ q16, int B, uint32_t hbase, uint32_t *th,
+                                          uint32_t (&ow)[2][12])
 {
     const int x0 = ux * kUnitCols;
     const int y0 = rp * 2;
     const int nvalid = FULL ? kUnitCols : (cg.W - x0);
-    uint32_t ow[2][12];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -483,14 +493,14 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
                 col_apply(cc, v3, t3);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    if (STATS) red_shared_inc(hbase + vb * 128u + (uint32_t)c * 32768u);
+                    if (STATS) hist_inc(hbase + vb * 128u, c);
                     const int bb = 3 * i + c;
                     ow[r][bb >> 2] = put_byte2(ow[r][bb >> 2], t3[c], bb & 3);
                 }
             } else {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    if (STATS) red_shared_inc(hbase + vb * 128u + (uint32_t)c * 32768u);
+                    if (STATS) hist_inc(hbase + vb * 128u, c);
                     uint32_t t = rg.aq[c] * vb + rg.cq[c];
                     t = t > 0xFFFFFFu ? 0xFFFFFFu : t;
                     const int bb = 3 * i + c;
@@ -500,17 +510,45 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
         }
         if constexpr (THUMBS) thumb_row<FULL>(th, cg, y0 + r, x0, nvalid, tv);
     }
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        uint8_t *dst = cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0;
-        if (FULL) {
-            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-            d4[0] = make_uint4(ow[r][0], ow[r][1], ow[r][2], ow[r][3]);
-            d4[1] = make_uint4(ow[r][4], ow[r][5], ow[r][6], ow[r][7]);
-            d4[2] = make_uint4(ow[r][8], ow[r][9], ow[r][10], ow[r][11]);
-        } else {
+    // a full unit's 48 bytes per row go out through store_unit; a ragged one
+    // writes its bytes here
+    if (!FULL) {
+        for (int r = 0; r < 2; ++r) {
+            uint8_t *dst = cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0;
             for (int b = 0; b < 3 * nvalid; ++b) dst[b] = (uint8_t)(ow[r][b >> 2] >> (8 * (b & 3)));
         }
+    }
+}
+
+// 256-bit store (32-byte aligned p).
+__device__ __forceinline__ void st_v8(uint8_t *p, const uint32_t (&w)[8])
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :: "l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
+// A full unit's two 48-byte rows, each as one 32-byte and one 16-byte store
+// chosen by the row's alignment: at a 32-byte boundary bytes 0-31 then
+// 32-47, 16 bytes past one bytes 16-47 then 0-15.  The 32-byte stores are
+// whole sectors, and the 16-byte halves of two neighbouring units (the
+// next lane's unit) share a sector and one store instruction, so the warp
+// writes whole sectors (16 bytes every 48 would split every sector between
+// two instructions).
+__device__ __forceinline__ void store_unit(const uint32_t (&ow)[2][12], bool full, uint8_t *dst0, int pitch)
+{
+    if (!full) return;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        uint8_t *a = dst0 + (size_t)r * pitch;
+        const bool odd = ((uintptr_t)a >> 4) & 1u;
+        uint32_t w8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w8[i] = odd ? ow[r][4 + i] : ow[r][i];
+        const uint4 w4 = odd ? make_uint4(ow[r][0], ow[r][1], ow[r][2], ow[r][3])
+                             : make_uint4(ow[r][8], ow[r][9], ow[r][10], ow[r][11]);
+        st_v8(a + (odd ? 16 : 0), w8);
+        *reinterpret_cast<uint4 *>(a + (odd ? 0 : 32)) = w4;
     }
 }
 
@@ -531,7 +569,7 @@ pass_b_kernel(const ArrayGeom g, const PassBArgs a)
 {
     extern __shared__ uint32_t sh[];
     uint32_t *th = sh + (STATS ? kHistWords : 0);   // [36][64][3] cell sums (THUMBS)
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const ConvConsts &k = g.conv;
     allow_next_launch();
     // balanced contiguous slices: q units each, the first r slices one more
@@ -568,17 +606,27 @@ pass_b_kernel(const ArrayGeom g, const PassBArgs a)
         int rp = first / upr, ux = first - rp * upr;
         const int srp = (int)blockDim.x / upr, sux = (int)blockDim.x - srp * upr;
         const int nloc = (int)(se - cg.unit_base);
+        // lane l of a warp handles unit base + l while that is below nloc
+        uint32_t ow[2][12];
         if (cg.fmt == RT_NV12) {
-            for (int local = first; local < nloc; local += blockDim.x) {
-                const uint8_t *yp = cg.y + (size_t)(2 * rp) * cg.y_pitch + ux * kUnitCols;
-                const uint4 Y0 = ld_stream(yp), Y1 = ld_stream(yp + cg.y_pitch);
-                const uint4 UV = ld_stream(cg.uv + (size_t)rp * cg.uv_pitch + ux * kUnitCols);
-                if (ux < full_units)
-                    unit_nv12<FIT, STATS, true, THUMBS>(cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg, sa0, sa1,
-                                                        sa2, Y0, Y1, UV);
-                else
-                    unit_nv12<FIT, STATS, false, THUMBS>(cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg, sa0, sa1,
-                                                         sa2, Y0, Y1, UV);
+            for (int base = first - lane; base < nloc; base += blockDim.x) {
+                bool full = false;
+                uint8_t *dst0 = nullptr;
+                if (base + lane < nloc) {
+                    const uint8_t *yp = cg.y + (size_t)(2 * rp) * cg.y_pitch + ux * kUnitCols;
+                    const uint4 Y0 = ld_stream(yp), Y1 = ld_stream(yp + cg.y_pitch);
+                    const uint4 UV = ld_stream(cg.uv + (size_t)rp * cg.uv_pitch + ux * kUnitCols);
+                    if (ux < full_units) {
+                        unit_nv12<FIT, STATS, true, THUMBS>(cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg, sa0, sa1,
+                                                            sa2, Y0, Y1, UV, ow);
+                        full = true;
+                        dst0 = cg.rgb + (size_t)(2 * rp) * cg.rgb_pitch + 3 * kUnitCols * ux;
+                    } else {
+                        unit_nv12<FIT, STATS, false, THUMBS>(cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg, sa0, sa1,
+                                                             sa2, Y0, Y1, UV, ow);
+                    }
+                }
+                store_unit(ow, full, dst0, cg.rgb_pitch);
                 ux += sux;
                 rp += srp;
                 if (ux >= upr) {
@@ -587,9 +635,19 @@ pass_b_kernel(const ArrayGeom g, const PassBArgs a)
                 }
             }
         } else {
-            for (int local = first; local < nloc; local += blockDim.x) {
-                if (ux < full_units) unit_mono<FIT, STATS, true, THUMBS>(cg, cam, rp, ux, a.q16, g.B, hbase, th);
-                else unit_mono<FIT, STATS, false, THUMBS>(cg, cam, rp, ux, a.q16, g.B, hbase, th);
+            for (int base = first - lane; base < nloc; base += blockDim.x) {
+                bool full = false;
+                uint8_t *dst0 = nullptr;
+                if (base + lane < nloc) {
+                    if (ux < full_units) {
+                        unit_mono<FIT, STATS, true, THUMBS>(cg, cam, rp, ux, a.q16, g.B, hbase, th, ow);
+                        full = true;
+                        dst0 = cg.rgb + (size_t)(2 * rp) * cg.rgb_pitch + 3 * kUnitCols * ux;
+                    } else {
+                        unit_mono<FIT, STATS, false, THUMBS>(cg, cam, rp, ux, a.q16, g.B, hbase, th, ow);
+                    }
+                }
+                store_unit(ow, full, dst0, cg.rgb_pitch);
                 ux += sux;
                 rp += srp;
                 if (ux >= upr) {
@@ -636,8 +694,8 @@ pass_b_kernel(const ArrayGeom g, const PassBArgs a)
 template <int FIT, bool STATS, bool THUMBS>
 cudaError_t launch_one(const ArrayGeom &g, const PassBArgs &a, int grid, int threads, cudaStream_t s)
 {
-    const size_t smem = (size_t)((STATS ? kHistWords : 0) + (THUMBS ? kThumbWords : 0)) * 4;
     if (threads > kMaxThreads<FIT, THUMBS>) threads = kMaxThreads<FIT, THUMBS>;
+    const size_t smem = (size_t)((STATS ? kHistWords : 0) + (THUMBS ? kThumbWords : 0)) * 4;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(threads);
@@ -655,13 +713,12 @@ template <int FIT>
 cudaError_t prepare_fit()
 {
     cudaError_t e;
-    const int full = (kHistWords + kThumbWords) * 4;
     if ((e = cudaFuncSetAttribute(pass_b_kernel<FIT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kHistWords * 4)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(pass_b_kernel<FIT, true, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   100)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(pass_b_kernel<FIT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  full)) != cudaSuccess) return e;
+                                  (kHistWords + kThumbWords) * 4)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(pass_b_kernel<FIT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kThumbWords * 4)) != cudaSuccess) return e;
     return cudaSuccess;

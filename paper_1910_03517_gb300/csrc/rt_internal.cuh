@@ -29,7 +29,7 @@ namespace rt {
 // sets the register budget): fewer leave registers on each SM for the
 // statistics chain of the next frame set to run beside pass B.
 #ifndef RT_PASS_B_RUN_THREADS
-#define RT_PASS_B_RUN_THREADS 384
+#define RT_PASS_B_RUN_THREADS 352
 #endif
 
 // The seam-map variants of pass B (per-column coefficients of both rows of a
@@ -105,6 +105,9 @@ struct PassAArgs {
     // for the next frame set
     uint32_t *clear_u32; size_t clear_u32_n;
     unsigned long long *clear_u64; size_t clear_u64_n;
+    // surrogate mode (nullptr otherwise): gate[0] = run the statistics,
+    // gate[1] = the motion test may use prev_luma
+    const int32_t *gate;
 };
 
 // Tables of the table-driven logarithm and exponential of the gain solve
@@ -153,6 +156,10 @@ struct SolveArgs {
     const int32_t *right_nbr;     // [K]
     const int32_t *cam_H;         // [K]
     SolveTopo topo;               // the same chains, by value
+    // surrogate mode: skip the fit unless gate[0] (nullptr: always fit); with
+    // fit_only the per-camera gain fit writes maps_new only
+    const int32_t *gate;
+    int32_t fit_only;
     // filled by launch_solve
     SolveTables tab;
     double one_m_alpha;           // 1 - alpha
@@ -183,7 +190,28 @@ struct CropArgs {
     const int32_t *count;     // device count of valid windows (nullptr: all n)
 };
 
+// A synthetic frame set painted on the device (k_synth.cu): the learned
+// surrogate's training and evaluation arrays.  Each camera sees its slice of
+// a panorama (sky above a wavy horizon, smooth gradients, low-frequency
+// sinusoids), scaled by its per-channel gain, with Gaussian noise, rounded to
+// 8 bits and encoded as BT.709 limited-range NV12 (chroma the mean of each
+// 2 x 2 block) or as 12-bit mono.
+struct SynthArgs {
+    uint8_t *y[RT_MAX_CAMERAS];         // Y plane (NV12) or 16-bit mono plane
+    uint8_t *uv[RT_MAX_CAMERAS];        // UV plane (NV12)
+    int32_t W[RT_MAX_CAMERAS], H[RT_MAX_CAMERAS], y_pitch[RT_MAX_CAMERAS], uv_pitch[RT_MAX_CAMERAS];
+    int32_t fmt[RT_MAX_CAMERAS], bits[RT_MAX_CAMERAS];
+    float x0[RT_MAX_CAMERAS];           // panorama column of the camera's first column
+    float gain[RT_MAX_CAMERAS][3];
+    float ph[16];                       // scene parameters in [0, 1)
+    float noise;                        // noise standard deviation (8-bit levels)
+    uint32_t key_lo, key_hi;            // noise counter key
+    uint32_t block_base[RT_MAX_CAMERAS + 1];   // 2 x 2 blocks before camera k
+    int32_t K;
+};
+
 // Launchers (each returns the launch's cudaError_t).
+cudaError_t launch_synth(const SynthArgs &a, cudaStream_t s);
 cudaError_t launch_pass_b(const ArrayGeom &g, const PassBArgs &a, int grid, int threads,
                           size_t smem, cudaStream_t s);
 cudaError_t pass_b_prepare(int threads, size_t *smem_bytes);
