@@ -56,8 +56,9 @@ def parse():
     ap.add_argument("--timing-events", default="pass_b", choices=["pass_b", "all", "none"],
                     help="CUDA events inside the timed graph: around pass B only (the roofline's "
                          "timing), around every pass, or none (no roofline timing)")
-    ap.add_argument("--surrogate-arrays", type=int, default=800,
-                    help="16-camera training arrays (x16 samples) for the surrogate report")
+    ap.add_argument("--surrogate-samples", type=int, default=200000,
+                    help="training samples (cameras of generated 16-camera frame sets) of the surrogate report")
+    ap.add_argument("--surrogate-heldout", type=int, default=10000, help="held-out samples of the surrogate report")
     return ap.parse_args()
 
 
@@ -315,60 +316,125 @@ def run_reference(args):
 # learned surrogate: gain error against the plain fit, and its speed
 # ---------------------------------------------------------------------------
 
+def time_graph(cams, frames, kw, net_path=None, reps=20):
+    """Device time per frame set of a captured ring of `frames` (after one
+    single submit and two untimed launches) for an array configured with kw;
+    with net_path the array's surrogate network is loaded from that
+    checkpoint first.  Returns (us per frame set, surrogate report or None)."""
+    import torch
+    from paper_1910_03517_gb300 import rt
+    a = rt.CameraArray(cams, **kw)
+    if net_path:
+        a.surrogate_load(net_path)
+    n = len(frames) - len(frames) % 6
+    a.submit_frames(frames[0], 0)
+    a.sync()
+    a.capture_sequence(frames[:n])
+    for _ in range(2):
+        a.launch_sequence()
+    a.sync()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda._sleep(400000)
+    e0.record(st)
+    for _ in range(reps):
+        a.launch_sequence()
+    a.stream_wait(st)
+    e1.record(st)
+    e1.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / (reps * n)
+    rep = a.surrogate_report() if kw.get("surrogate_mode") else None
+    a.close()
+    return us, rep
+
+
 def surrogate_report(args):
+    """The learned surrogate of the 16-camera array (config 4): trained by
+    rt_surrogate_train on n samples of the array's own generated frame sets
+    (labels: the array's plain fit), evaluated on held-out ones, then run
+    inside the pipeline (surrogate mode) beside the plain schedules; and the
+    same modes timed on the headline array."""
     import numpy as np
     import torch
     from paper_1910_03517_gb300 import rt, surrogate as sg, synth
     n_cams, W, H = 16, 512, 288
-    t0 = time.perf_counter()
-    Xtr, Ytr = sg.make_dataset(args.surrogate_arrays, seed=11, n_cams=n_cams, width=W, height=H)
-    Xte, Yte = sg.make_dataset(100, seed=12, n_cams=n_cams, width=W, height=H)
-    t_data = time.perf_counter() - t0
-    net = rt.GainMLP()
-    net.set_params(sg.init_params(0))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    losses = sg.train(net, Xtr, Ytr, epochs=6, lr=1e-3)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    pred = sg.regauge(sg.predict(net, Xte), n_cams)
-    lab = Yte.cpu().numpy()
-    err = sg.gain_error(pred, lab)
-    per_array = err.reshape(-1, n_cams).max(1)
-    err_id = sg.gain_error(np.zeros_like(lab), lab)
-    # speed: inference + judge on one array vs the plain statistics chain of that array
-    wl = sg.training_workload(n_cams, W, H, seed=99)
-    arr = rt.CameraArray(wl.cams, flags=rt.RT_FLAG_THUMBNAILS)
-    fs = synth.frame_set(wl, 0, device="cuda")
-    arr.profile(True)
-    for i in range(20):
-        arr.submit_frames(fs, i)
-    prof = arr.get_profile()
-    arr.profile(False)
-    for _ in range(3):
-        arr.surrogate_predict(net)
-    reps = 20
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        _, jerr = arr.surrogate_predict(net)
-    t_pred = (time.perf_counter() - t0) / reps
+    cams = sg.training_workload(n_cams, W, H, seed=0).cams
+    flags = rt.RT_FLAG_THUMBNAILS | rt.RT_FLAG_FRAME_STATS
+    arr = rt.CameraArray(cams, flags=flags)
+    n_train, n_held, epochs = args.surrogate_samples, args.surrogate_heldout, 6
+    losses, secs = [], []
+    for ep in range(epochs):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses.append(arr.surrogate_train(n_train, 256, 1e-3 * 0.5 ** ep, seed=11))
+        secs.append(time.perf_counter() - t0)
+    err, err_id = arr.surrogate_evaluate(n_held, seed=12)
+    path = os.path.join(tempfile.gettempdir(), "rt_surrogate_%d.bin" % os.getpid())
+    arr.surrogate_save(path)
     arr.close()
-    seq = quality_sequence(net, n_cams, W, H)
-    net.close()
-    return {
-        "sequence": seq,
-        "train_samples": int(Xtr.shape[0]), "train_epochs": 6, "data_seconds": round(t_data, 1),
-        "train_seconds": round(t_train, 2), "train_samples_per_s": round(6 * Xtr.shape[0] / t_train),
-        "final_loss": float(np.mean(losses[-10:])),
-        "heldout_cameras": int(lab.shape[0]),
+    per_array = err.max(1)
+    steps = len(losses[0])
+    out = {
+        "train_samples": int(n_train), "heldout_samples": int(err.size), "epochs": epochs, "batch": 256,
+        "first_epoch_seconds_incl_generation": round(secs[0], 2),
+        "train_seconds_per_epoch": round(float(np.mean(secs[1:])), 3),
+        "train_samples_per_s": round(n_train / float(np.mean(secs[1:]))),
+        "train_step_us": round(1e6 * float(np.mean(secs[1:])) / steps, 1),
+        "loss_first_steps": float(np.mean(losses[0][:5])), "loss_last_epoch": float(np.mean(losses[-1])),
         "median_gain_err": float(np.median(err)), "p99_gain_err": float(np.percentile(err, 99)),
         "median_gain_err_uncorrected": float(np.median(err_id)),
         "fallback_rate_2pct": float(np.mean(per_array > 0.02)),
-        "predict_plus_judge_ms_16cams": round(1e3 * t_pred, 3),
-        "plain_chain_ms_16cams": round((prof["pass_a_ms"] + prof["solve_ms"]) / max(1, prof["frame_sets"]), 4),
-        "note": ("surrogate = thumbnail features + tcgen05 MLP + re-gauge + judge (host-synchronous call); "
-                 "plain chain = band statistics + FP64 solve (device time, overlapped with pass B in the pipeline)"),
     }
+    # the modes of the pipeline on a 16-camera sequence (moving object, gains
+    # drifting 1 % a frame), ring of 24 frame sets in a captured graph
+    wl = sg.training_workload(n_cams, W, H, seed=123)
+    wl.moving_object, wl.gain_walk, wl.frames = True, 0.01, 24
+    frames = [synth.frame_set(wl, t, device="cuda") for t in range(24)]
+    modes = {}
+    base = dict(flags=flags)
+    for name, kw, net in (("current", dict(base), None),
+                          ("lagged", dict(base, schedule=rt.RT_SCHED_LAGGED), None),
+                          ("surrogate", dict(base, surrogate_mode=1, judge_every=8, fallback_tol=0.02), path),
+                          ("surrogate_prediction_applied", dict(base, surrogate_mode=1, judge_every=8,
+                                                                 fallback_tol=1e9), path),
+                          ("surrogate_fallback", dict(base, surrogate_mode=1, judge_every=8, fallback_tol=0.0), path)):
+        us, rep = time_graph(cams, frames, kw, net)
+        modes[name] = {"us_per_frame_set": round(us, 2)}
+        if rep:
+            modes[name].update({k: rep[k] for k in ("frame_sets", "predicted", "plain", "judged", "judged_failed")})
+    out["pipeline_16cams_512x288"] = modes
+    out["sequence"] = quality_sequence(path, n_cams, W, H)
+    # the headline array: a network trained briefly on its own geometry (its
+    # accuracy is not the point), the same modes timed
+    tw = workload("tower12")
+    tarr = rt.CameraArray(tw.cams, flags=flags)
+    tarr.surrogate_train(12 * 1024, 256, 1e-3, seed=21)
+    tpath = path + ".tower12"
+    tarr.surrogate_save(tpath)
+    tarr.close()
+    tframes = [synth.frame_set(tw, t, device="cuda") for t in range(18)]
+    tm = {}
+    for name, kw, net in (("current_no_thumbnails", dict(flags=rt.RT_FLAG_FRAME_STATS), None),
+                          ("current", dict(base), None),
+                          ("surrogate_prediction_applied", dict(base, surrogate_mode=1, judge_every=8,
+                                                                 fallback_tol=1e9), tpath),
+                          ("surrogate_fallback", dict(base, surrogate_mode=1, judge_every=8, fallback_tol=0.0), tpath)):
+        us, rep = time_graph(tw.cams, tframes, kw, net)
+        tm[name] = {"us_per_frame_set": round(us, 2)}
+        if rep:
+            tm[name].update({k: rep[k] for k in ("predicted", "plain", "judged")})
+    out["pipeline_tower12"] = tm
+    del tframes, frames
+    for f in (path, tpath):
+        try:
+            os.remove(f)
+        except OSError:
+            pass
+    out["note"] = ("surrogate mode: prediction from the previous frame set's thumbnails through the tcgen05 MLP on "
+                   "the device, the plain fit as judge every 8th frame set and as fallback above 2 %; all captured "
+                   "in one graph with the rest of the pipeline; the prediction needs the previous frame set's "
+                   "pass B, so it cannot overlap it as the band statistics do")
+    return out
 
 
 def detection_frames(frames=60, n_obj=200, classes=8, seed=21):
@@ -477,35 +543,36 @@ def track_report(oracle_seconds=6.0):
                              "same_keep_and_ids": bool(same)}}
 
 
-def quality_sequence(net, n_cams, W, H, frames=30):
+def quality_sequence(net_path, n_cams, W, H, frames=30):
     """A moving object crossing seams, camera gains drifting 1 % a frame:
-    frame-to-frame jitter of the log-gains (mean |ln g_t - ln g_{t-1}| over
-    cameras and channels) and the mean seam cost of the corrected output
-    (Eq. gradientcost) under the CURRENT and LAGGED schedules, and the jitter
-    of the surrogate's raw predictions on the same frames."""
+    frame-to-frame jitter of the smoothed log-gains (mean |ln g_t - ln
+    g_{t-1}| over cameras and channels) and the mean seam cost of the
+    corrected output (Eq. gradientcost) under the CURRENT and LAGGED
+    schedules and in surrogate mode (judge every 8th frame set, fallback
+    above 2 %), with what the surrogate mode did."""
     import numpy as np
     from paper_1910_03517_gb300 import rt, surrogate as sg, synth
     wl = sg.training_workload(n_cams, W, H, seed=123)
     wl.moving_object, wl.gain_walk, wl.frames = True, 0.01, frames
     out = {"frames": frames, "cameras": n_cams, "size": "%dx%d" % (W, H)}
-    for name, sched in (("current", rt.RT_SCHED_CURRENT), ("lagged", rt.RT_SCHED_LAGGED)):
-        arr = rt.CameraArray(wl.cams, flags=rt.RT_FLAG_THUMBNAILS | rt.RT_FLAG_SEAM_COST, schedule=sched)
-        logs, costs, preds = [], [], []
+    flags = rt.RT_FLAG_THUMBNAILS | rt.RT_FLAG_SEAM_COST
+    for name, kw in (("current", dict(schedule=rt.RT_SCHED_CURRENT)), ("lagged", dict(schedule=rt.RT_SCHED_LAGGED)),
+                     ("surrogate", dict(surrogate_mode=1, judge_every=8, fallback_tol=0.02))):
+        arr = rt.CameraArray(wl.cams, flags=flags, **kw)
+        if name == "surrogate":
+            arr.surrogate_load(net_path)
+        logs, costs = [], []
         for t in range(frames):
             arr.submit_frames(synth.frame_set(wl, t, device="cuda"), t)
             maps, _ = arr.get_gains()
             logs.append(np.log(maps[:, 0, 0, :, 0]))
             costs.append(float(np.mean([c for (_, _, c) in arr.seam_costs()])))
-            if sched == rt.RT_SCHED_CURRENT:
-                p, _ = arr.surrogate_predict(net)
-                preds.append(np.log(p[:, 0, 0, :, 0]))
-        arr.close()
         out[name] = {"gain_jitter": float(np.mean(np.abs(np.diff(np.stack(logs), axis=0)))),
                      "seam_cost": float(np.mean(costs[1:]))}
-        if preds:
-            out["surrogate_raw_jitter"] = float(np.mean(np.abs(np.diff(np.stack(preds), axis=0))))
-    out["note"] = ("plain gains are the smoothed estimate (alpha 0.05); the surrogate's are its raw "
-                   "per-frame predictions (it is not applied inside the pipeline)")
+        if name == "surrogate":
+            rep = arr.surrogate_report()
+            out[name].update({k: rep[k] for k in ("predicted", "plain", "judged", "judged_failed", "max_error")})
+        arr.close()
     return out
 
 

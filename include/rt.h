@@ -122,7 +122,21 @@ typedef struct {
  *                      windows step by attn_window / 2;
  *   attn_min_on        on-pixels (|Y_t - Y_{t-1}| > motion_threshold) a
  *                      window needs to be proposed, >= 1 (655, 1 % of 256^2);
- *   attn_max           proposals kept per frame set, 1..4096 (256). */
+ *   attn_max           proposals kept per frame set, 1..4096 (256);
+ *   surrogate_mode     0: the gains are fitted every frame set (the paper's
+ *                      method); 1: the learned surrogate (rt_surrogate.h)
+ *                      predicts them from the previous frame set's
+ *                      thumbnails and the fit runs only as its judge and
+ *                      fallback -- needs RT_FIT_GLOBAL, one block,
+ *                      RT_FLAG_THUMBNAILS, the current schedule and a network
+ *                      (rt_surrogate_train or rt_surrogate_load) before the
+ *                      first submit;
+ *   judge_every        surrogate mode: the fit judges the prediction every
+ *                      judge_every-th frame set of a sequence (>= 1; 8);
+ *   fallback_tol       surrogate mode: a judged prediction whose largest
+ *                      |g_pred / g_fit - 1| exceeds this (>= 0; 0.02) is
+ *                      replaced by the fit, which stays applied (and judges
+ *                      every frame set) until a judgement passes. */
 typedef struct {
     int32_t num_cameras;
     const rt_camera_desc *cams;
@@ -133,6 +147,8 @@ typedef struct {
     int32_t max_crops, crop_size;
     int32_t flags;
     int32_t attn_window, attn_min_on, attn_max;
+    int32_t surrogate_mode, judge_every;
+    double fallback_tol;
 } rt_array_params;
 
 #define RT_FLAG_FRAME_STATS 1   /* whole-frame histograms of every camera (S2 iii) */
@@ -160,7 +176,8 @@ typedef struct rt_handle rt_handle;
 
 /* Fill p with the defaults (S = 32, B = 1, per-camera gains, current
  * schedule, T = 24, min_valid = 64, BT.709, alpha = 0.05, lambda = 1e-6,
- * gains in [1/4, 4], no crops, frame statistics on).  cams is left NULL. */
+ * gains in [1/4, 4], no crops, frame statistics on, no surrogate mode,
+ * judge_every = 8, fallback_tol = 0.02).  cams is left NULL. */
 void rt_default_params(rt_array_params *p);
 
 /* Validate the configuration, allocate every device buffer the array needs

@@ -6,19 +6,25 @@
 // log-gains of the per-camera gain fit.
 //
 // A training step for a batch of 256 thumbnails (M = 256):
-//   fwd1  H1 = relu(X W1^T + b1)        GEMM 256x256x6912, epilogue writes H1, H1^T
+//   fwd1  H1 = relu(X W1^T + b1)        GEMM 256x256x6912 split over K in 27
+//                                       pieces of 256 (108 CTAs), partial sums
+//                                       reduced in a fixed order with the bias
+//                                       and ReLU, writing H1 and H1^T
 //   fwd2  H2 = relu(H1 W2^T + b2)       GEMM 256x256x256
-//   head  y = H2 W3^T + b3, loss, dy, dW3, db3, dZ2 = (dy W3) * [H2 > 0]  (CUDA cores)
+//   head  y = H2 W3^T + b3, e = y - t, dZ2 = (dy W3) * [H2 > 0]  (CUDA cores)
+//         loss, dW3, db3: sums over the batch in a fixed order
 //   dW2 = dZ2^T H1                      GEMM 256x256x256  (A = dZ2^T, B = H1^T)
 //   dZ1 = (dZ2 W2) * [H1 > 0]           GEMM 256x256x256  (A = dZ2,  B = W2^T)
 //   dW1 = dZ1^T X                       GEMM 256x6912x256 (A = dZ1^T, B = X^T)
-//   db1, db2 (batch sums), Adam over all parameters, BF16 copies of W1, W2, W2^T, W3.
+//   db1, db2 (batch sums), Adam over all parameters, BF16 copies of W1, W2, W2^T.
+// No floating-point atomics anywhere: a step is bit-for-bit reproducible.
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "rt_internal.cuh"
+#include "mlp_internal.cuh"
 #include "tc_gemm.cuh"
 #include "../../include/rt_surrogate.h"
 #include "../../include/rt_check.h"
@@ -35,6 +41,8 @@ constexpr size_t OFF_W1 = 0, OFF_B1 = OFF_W1 + (size_t)D_H * D_IN, OFF_W2 = OFF_
                  OFF_B2 = OFF_W2 + (size_t)D_H * D_H, OFF_W3 = OFF_B2 + D_H, OFF_B3 = OFF_W3 + (size_t)D_OUT * D_H,
                  N_PARAMS = OFF_B3 + D_OUT;
 constexpr int kBN = 128;
+constexpr int kSplit1 = 27;        // K pieces of the first layer's forward GEMM (6912 = 27 x 256)
+static_assert(D_IN % (kSplit1 * tc::kBK) == 0, "split of the first layer");
 
 using bf16 = __nv_bfloat16;
 
@@ -84,24 +92,66 @@ struct EpiStore {               // out[row][col] = v (FP32)
     }
 };
 
+struct EpiPartial {             // part[z][row][col] = v (FP32), z = the K piece (blockIdx.z)
+    float *part; int M;
+    __device__ void operator()(int row, int col0, const float *v) const
+    {
+        float4 *d = reinterpret_cast<float4 *>(part + ((size_t)blockIdx.z * M + row) * D_H + col0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    }
+};
+
+// One 128 x kBN tile of D = A B^T over the K piece blockIdx.z of K / gridDim.z.
 template <class Epi>
 __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                       const __grid_constant__ CUtensorMap tmB, int K, Epi epi,
                                                       int *err)
 {
-    tc::gemm_tile<kBN>(&tmA, &tmB, K, epi, err);
+    const int kz = K / (int)gridDim.z;
+    tc::gemm_tile<kBN>(&tmA, &tmB, (int)blockIdx.z * kz, kz, epi, err);
 }
 
 // ---------------------------------------------------------------------------
 // CUDA-core kernels
 // ---------------------------------------------------------------------------
 
-// Output layer, loss and its backward for one batch row per CTA (256 threads).
+// Sum of the first layer's K pieces in a fixed order, + bias, ReLU, BF16:
+// H [M][256] row-major and (optionally) HT [256][ldT] transposed.  One
+// thread per row and 4 consecutive columns.
+__global__ void __launch_bounds__(256) split_relu_kernel(const float *__restrict__ part, int M,
+                                                         const float *__restrict__ bias, bf16 *__restrict__ H,
+                                                         bf16 *__restrict__ HT, int ldT)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M * (D_H / 4)) return;
+    const int row = t / (D_H / 4), c0 = (t % (D_H / 4)) * 4;
+    const size_t zs = (size_t)M * D_H / 4;
+    const float4 *p = reinterpret_cast<const float4 *>(part + (size_t)row * D_H + c0);
+    float4 acc = p[0];
+#pragma unroll
+    for (int z = 1; z < kSplit1; ++z) {
+        const float4 v = p[z * zs];
+        acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    const float a[4] = {acc.x, acc.y, acc.z, acc.w};
+    bf16 h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __float2bfloat16_rn(fmaxf(a[i] + bias[c0 + i], 0.0f));
+    *reinterpret_cast<uint2 *>(H + (size_t)row * D_H + c0) = *reinterpret_cast<const uint2 *>(h);
+    if (HT) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) HT[(size_t)(c0 + i) * ldT + row] = h[i];
+    }
+}
+
+// Output layer and the start of its backward for one batch row per CTA (256
+// threads): y = H2 W3^T + b3; with gradients, e = y - t for the n_valid real
+// rows (0 for padding rows) and dZ2 = ((2 e / (3 n)) W3) * [H2 > 0].
 __global__ void __launch_bounds__(256) head_kernel(const bf16 *__restrict__ H2, const float *__restrict__ P,
                                                    const float *__restrict__ T, int n_valid, float *__restrict__ Y,
-                                                   float *__restrict__ G, bf16 *__restrict__ dZ2,
-                                                   bf16 *__restrict__ dZ2T, float *__restrict__ loss, int Mb,
-                                                   int want_grad)
+                                                   float *__restrict__ Eo, bf16 *__restrict__ dZ2,
+                                                   bf16 *__restrict__ dZ2T, int Mb, int want_grad)
 {
     const int b = blockIdx.x, i = threadIdx.x;
     __shared__ float red[D_OUT][8];
@@ -124,11 +174,10 @@ __global__ void __launch_bounds__(256) head_kernel(const bf16 *__restrict__ H2, 
         const float y = s + P[OFF_B3 + i];
         Y[b * D_OUT + i] = y;
         float d = 0.0f;
-        if (want_grad && b < n_valid) {
-            const float e = y - T[b * D_OUT + i];
-            atomicAdd(loss, e * e / (float)(n_valid * D_OUT));
+        if (want_grad) {
+            const float e = b < n_valid ? y - T[b * D_OUT + i] : 0.0f;
+            Eo[b * D_OUT + i] = e;
             d = 2.0f * e / (float)(n_valid * D_OUT);
-            atomicAdd(&G[OFF_B3 + i], d);
         }
         dy[i] = d;
     }
@@ -136,13 +185,71 @@ __global__ void __launch_bounds__(256) head_kernel(const bf16 *__restrict__ H2, 
     if (!want_grad) return;
     float g = 0.0f;
 #pragma unroll
-    for (int o = 0; o < D_OUT; ++o) {
-        atomicAdd(&G[OFF_W3 + o * D_H + i], dy[o] * h);
-        g += dy[o] * w[o];
-    }
+    for (int o = 0; o < D_OUT; ++o) g += dy[o] * w[o];
     const bf16 z = __float2bfloat16_rn(h > 0.0f ? g : 0.0f);
     dZ2[(size_t)b * D_H + i] = z;
     dZ2T[(size_t)i * Mb + b] = z;
+}
+
+// Batch sums of the output layer, each in a fixed order (no atomics), with
+// dy = 2 e / (3 n) rounded as in the head: dW3[o][i] = sum_b dy[b][o] H2[b][i]
+// (thread i), db3[o] = sum_b dy[b][o] and (CTA 0) loss = sum_b,o e^2 / (3 n),
+// both by a fixed tree over the threads.  Grid of 3 CTAs (o) x 256 threads.
+__global__ void __launch_bounds__(256) head_sums_kernel(const bf16 *__restrict__ H2, const float *__restrict__ Eo,
+                                                        int n_valid, float *__restrict__ G, float *__restrict__ loss)
+{
+    __shared__ float s_db[256], s_l[256];
+    const int o = blockIdx.x, i = threadIdx.x;
+    const float den = (float)(n_valid * D_OUT);
+    float acc = 0.0f;
+#pragma unroll 8
+    for (int b = 0; b < n_valid; ++b) acc += (2.0f * Eo[b * D_OUT + o] / den) * __bfloat162float(H2[(size_t)b * D_H + i]);
+    G[OFF_W3 + o * D_H + i] = acc;
+    float l = 0.0f;
+    if (i < n_valid) {
+#pragma unroll
+        for (int q = 0; q < D_OUT; ++q) {
+            const float e = Eo[i * D_OUT + q];
+            l += e * e;
+        }
+    }
+    s_db[i] = i < n_valid ? 2.0f * Eo[i * D_OUT + o] / den : 0.0f;
+    s_l[i] = l;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (i < w) {
+            s_db[i] += s_db[i + w];
+            s_l[i] += s_l[i + w];
+        }
+        __syncthreads();
+    }
+    if (i == 0) {
+        G[OFF_B3 + o] = s_db[0];
+        if (o == 0 && loss) *loss = s_l[0] / den;
+    }
+}
+
+// A training batch gathered from a training set: X[b] = data_x[idx[b]],
+// X^T, T[b] = data_t[idx[b]] for b < n; rows n .. 255 are zero.  Tiles of
+// 32 rows x 32 features through shared memory (coalesced X^T stores).
+__global__ void gather_kernel(const bf16 *__restrict__ data_x, const float *__restrict__ data_t,
+                              const int32_t *__restrict__ idx, int n, bf16 *__restrict__ X, bf16 *__restrict__ XT,
+                              float *__restrict__ T)
+{
+    __shared__ bf16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        const bf16 v = r < n ? data_x[(size_t)idx[r] * D_IN + c] : __float2bfloat16_rn(0.0f);
+        t[i][threadIdx.x] = v;
+        X[(size_t)r * D_IN + c] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.y == 0) {
+        const int r = r0 + threadIdx.x;
+        for (int q = 0; q < D_OUT; ++q) T[r * D_OUT + q] = r < n ? data_t[(size_t)idx[r] * D_OUT + q] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) XT[(size_t)(c0 + i) * MAXB + r0 + threadIdx.x] = t[threadIdx.x][i];
 }
 
 // bias gradient: db[j] = sum over the batch of dZ^T[j][b]  (one warp per j)
@@ -291,7 +398,7 @@ struct rt_mlp {
     bf16 *W1b = nullptr, *W2b = nullptr, *W2bT = nullptr;
     bf16 *X = nullptr, *XT = nullptr, *H1 = nullptr, *H1T = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ2T = nullptr,
          *dZ1T = nullptr;
-    float *T = nullptr, *Y = nullptr, *loss = nullptr;
+    float *T = nullptr, *Y = nullptr, *Eo = nullptr, *loss = nullptr, *part = nullptr;
     int *err = nullptr;
     int64_t steps = 0;
     // tensor maps (fixed buffers)
@@ -315,75 +422,181 @@ rt_status mfail(rt_mlp *m, rt_status s, const std::string &msg)
                          std::string(#call) + ": " + cudaGetErrorString(e_));                         \
     } while (0)
 
+#define CE(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return e_;                                                             \
+    } while (0)
+
+// The GEMM kernels' dynamic shared memory limit is set once, in rt_mlp_create.
 template <class Epi>
-cudaError_t run_gemm(rt_mlp *m, const CUtensorMap &A, const CUtensorMap &B, int M, int N, int K, const Epi &epi)
+cudaError_t gemm_attr()
 {
-    const size_t smem = tc::Smem<kBN>::kBytes;
-    static bool attr = false;
-    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    (void)attr;
-    dim3 grid(N / kBN, M / tc::kBM);
-    gemm_kernel<Epi><<<grid, 128, smem, m->s>>>(A, B, K, epi, m->err);
+    return cudaFuncSetAttribute(gemm_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc::Smem<kBN>::kBytes);
+}
+
+template <class Epi>
+cudaError_t run_gemm(rt_mlp *m, const CUtensorMap &A, const CUtensorMap &B, int M, int N, int K, int splits,
+                     const Epi &epi, cudaStream_t st)
+{
+    dim3 grid(N / kBN, M / tc::kBM, splits);
+    gemm_kernel<Epi><<<grid, 128, tc::Smem<kBN>::kBytes, st>>>(A, B, K, epi, m->err);
     return cudaGetLastError();
 }
 
-rt_status check_err(rt_mlp *m)
+// Forward of Mb rows of m->X (n_valid real ones) and, with grad, the backward
+// into m->G and the batch loss into *loss_out (device; may be null).
+cudaError_t fwd_bwd(rt_mlp *m, int Mb, int n_valid, bool grad, float *loss_out, cudaStream_t st)
 {
-    int e = 0;
-    MC(m, cudaMemcpyAsync(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->s));
-    MC(m, cudaStreamSynchronize(m->s));
-    if (e) return mfail(m, RT_ERR_TIMEOUT, "a tensor-core GEMM gave up waiting (code " + std::to_string(e) + ")");
-    return RT_OK;
-}
-
-// forward (and, with T, backward) of Mb rows already in m->X (n_valid real rows)
-rt_status fwd_bwd(rt_mlp *m, int Mb, int n_valid, bool grad)
-{
-    EpiReluBias e1{m->P + OFF_B1, m->H1, D_H, grad ? m->H1T : nullptr, MAXB};
-    MC(m, run_gemm(m, m->mX, m->mW1, Mb, D_H, D_IN, e1));
-    EpiReluBias e2{m->P + OFF_B2, m->H2, D_H, nullptr, 0};
-    MC(m, run_gemm(m, m->mH1, m->mW2, Mb, D_H, D_H, e2));
-    if (grad) {
-        MC(m, cudaMemsetAsync(m->G, 0, N_PARAMS * sizeof(float), m->s));
-        MC(m, cudaMemsetAsync(m->loss, 0, sizeof(float), m->s));
+    EpiPartial ep{m->part, Mb};
+    CE(run_gemm(m, m->mX, m->mW1, Mb, D_H, D_IN, kSplit1, ep, st));
+    {
+        const int threads = Mb * (D_H / 4);
+        split_relu_kernel<<<(threads + 255) / 256, 256, 0, st>>>(m->part, Mb, m->P + OFF_B1, m->H1,
+                                                                 grad ? m->H1T : nullptr, MAXB);
+        CE(cudaGetLastError());
     }
-    head_kernel<<<Mb, D_H, 0, m->s>>>(m->H2, m->P, m->T, n_valid, m->Y, m->G, m->dZ2, m->dZ2T, m->loss, MAXB,
-                                      grad ? 1 : 0);
-    MC(m, cudaGetLastError());
-    if (!grad) return RT_OK;
+    EpiReluBias e2{m->P + OFF_B2, m->H2, D_H, nullptr, 0};
+    CE(run_gemm(m, m->mH1, m->mW2, Mb, D_H, D_H, 1, e2, st));
+    head_kernel<<<grad ? MAXB : Mb, D_H, 0, st>>>(m->H2, m->P, m->T, n_valid, m->Y, m->Eo, m->dZ2, m->dZ2T, MAXB,
+                                                  grad ? 1 : 0);
+    CE(cudaGetLastError());
+    if (!grad) return cudaSuccess;
+    head_sums_kernel<<<D_OUT, D_H, 0, st>>>(m->H2, m->Eo, n_valid, m->G, loss_out);
+    CE(cudaGetLastError());
     EpiStore s2{m->G + OFF_W2, D_H};
-    MC(m, run_gemm(m, m->mdZ2T, m->mH1T, D_H, D_H, MAXB, s2));
+    CE(run_gemm(m, m->mdZ2T, m->mH1T, D_H, D_H, MAXB, 1, s2, st));
     EpiMaskT mk{m->H1, D_H, m->dZ1T, MAXB};
-    MC(m, run_gemm(m, m->mdZ2, m->mW2T, Mb, D_H, D_H, mk));
+    CE(run_gemm(m, m->mdZ2, m->mW2T, MAXB, D_H, D_H, 1, mk, st));
     EpiStore s1{m->G + OFF_W1, D_IN};
-    MC(m, run_gemm(m, m->mdZ1T, m->mXT, D_H, D_IN, MAXB, s1));
-    bias_grad_kernel<<<D_H / 8, 256, 0, m->s>>>(m->dZ1T, MAXB, n_valid, m->G + OFF_B1, D_H);
-    bias_grad_kernel<<<D_H / 8, 256, 0, m->s>>>(m->dZ2T, MAXB, n_valid, m->G + OFF_B2, D_H);
-    MC(m, cudaGetLastError());
-    return RT_OK;
+    CE(run_gemm(m, m->mdZ1T, m->mXT, D_H, D_IN, MAXB, 1, s1, st));
+    bias_grad_kernel<<<D_H / 8, 256, 0, st>>>(m->dZ1T, MAXB, n_valid, m->G + OFF_B1, D_H);
+    bias_grad_kernel<<<D_H / 8, 256, 0, st>>>(m->dZ2T, MAXB, n_valid, m->G + OFF_B2, D_H);
+    return cudaGetLastError();
 }
 
-rt_status load_batch(rt_mlp *m, const void *x, const float *t, int n, int Mb)
+cudaError_t adam(rt_mlp *m, double lr, cudaStream_t st)
+{
+    m->steps += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = (float)(1.0 - std::pow(0.9, (double)m->steps)), c2 = (float)(1.0 - std::pow(0.999, (double)m->steps));
+    adam_kernel<<<1024, 256, 0, st>>>(m->P, m->G, m->Mm, m->Vv, (float)lr, b1, b2, 1e-8f, c1, c2, m->W1b, m->W2b,
+                                      m->W2bT);
+    return cudaGetLastError();
+}
+
+// A caller's batch (host or device memory) into X (and X^T, T for training);
+// padding rows are zero.
+rt_status load_batch(rt_mlp *m, const void *x, const float *t, int n)
 {
     MC(m, cudaMemsetAsync(m->X, 0, (size_t)MAXB * D_IN * 2, m->s));
     MC(m, cudaMemcpyAsync(m->X, x, (size_t)n * D_IN * 2, cudaMemcpyDefault, m->s));
     if (t) {
         MC(m, cudaMemsetAsync(m->T, 0, (size_t)MAXB * D_OUT * 4, m->s));
         MC(m, cudaMemcpyAsync(m->T, t, (size_t)n * D_OUT * 4, cudaMemcpyDefault, m->s));
-        // X^T for the weight gradient of the first layer (all MAXB columns; padding is zero)
         dim3 g(D_IN / 32, MAXB / 32), b(32, 8);
         transpose_kernel<<<g, b, 0, m->s>>>(m->X, MAXB, D_IN, m->XT);
         MC(m, cudaGetLastError());
-        // dZ rows of padded batch entries must be zero: cleared here, left zero by the head kernel
-        MC(m, cudaMemsetAsync(m->dZ2, 0, (size_t)MAXB * D_H * 2, m->s));
-        MC(m, cudaMemsetAsync(m->dZ2T, 0, (size_t)MAXB * D_H * 2, m->s));
     }
-    (void)Mb;
     return RT_OK;
 }
 
+rt_status check_err(rt_mlp *m)
+{
+    std::string msg;
+    rt_status s = rt::mlp_check(m, m->s, &msg);
+    if (s != RT_OK) m->msg = msg;
+    return s;
+}
+
 }  // namespace
+
+namespace rt {
+
+__nv_bfloat16 *mlp_input(rt_mlp *m) { return m->X; }
+const float *mlp_output(const rt_mlp *m) { return m->Y; }
+int64_t mlp_steps(const rt_mlp *m) { return m->steps; }
+
+cudaError_t mlp_forward_async(rt_mlp *m, int n, cudaStream_t s)
+{
+    if (n < 1 || n > MAXB) return cudaErrorInvalidValue;
+    return fwd_bwd(m, n <= tc::kBM ? tc::kBM : MAXB, n, false, nullptr, s);
+}
+
+cudaError_t mlp_train_batch_async(rt_mlp *m, const __nv_bfloat16 *data_x, const float *data_t, const int32_t *idx,
+                                  int n, double lr, float *loss_out, cudaStream_t s)
+{
+    if (n < 1 || n > MAXB) return cudaErrorInvalidValue;
+    dim3 g(D_IN / 32, MAXB / 32), b(32, 8);
+    gather_kernel<<<g, b, 0, s>>>(data_x, data_t, idx, n, m->X, m->XT, m->T);
+    CE(cudaGetLastError());
+    CE(fwd_bwd(m, MAXB, n, true, loss_out, s));
+    return adam(m, lr, s);
+}
+
+rt_status mlp_check(rt_mlp *m, cudaStream_t s, std::string *msg)
+{
+    int e = 0;
+    cudaError_t r = cudaMemcpyAsync(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(s);
+    if (r != cudaSuccess) {
+        if (msg) *msg = std::string("surrogate network: ") + cudaGetErrorString(r);
+        return RT_ERR_CUDA;
+    }
+    if (e) {
+        if (msg) *msg = "a tensor-core GEMM gave up waiting (code " + std::to_string(e) + ")";
+        return RT_ERR_TIMEOUT;
+    }
+    return RT_OK;
+}
+
+// Blob: magic, version, parameter count, step count, then P, Adam m, Adam v.
+constexpr uint32_t kNetMagic = 0x534E5452u;   // "RTNS"
+constexpr uint32_t kNetVersion = 1;
+
+rt_status mlp_serialize(rt_mlp *m, cudaStream_t s, std::vector<uint8_t> *out)
+{
+    const size_t head = 4 + 4 + 8 + 8, body = (size_t)N_PARAMS * 4;
+    out->assign(head + 3 * body, 0);
+    uint8_t *p = out->data();
+    const uint64_t np = N_PARAMS;
+    const int64_t st = m->steps;
+    memcpy(p, &kNetMagic, 4);
+    memcpy(p + 4, &kNetVersion, 4);
+    memcpy(p + 8, &np, 8);
+    memcpy(p + 16, &st, 8);
+    if (cudaMemcpyAsync(p + head, m->P, body, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(p + head + body, m->Mm, body, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(p + head + 2 * body, m->Vv, body, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return RT_ERR_CUDA;
+    return RT_OK;
+}
+
+rt_status mlp_deserialize(rt_mlp *m, cudaStream_t s, const uint8_t *p, size_t n)
+{
+    const size_t head = 4 + 4 + 8 + 8, body = (size_t)N_PARAMS * 4;
+    if (n != head + 3 * body) return RT_ERR_INVALID;
+    uint32_t magic = 0, ver = 0;
+    uint64_t np = 0;
+    int64_t st = 0;
+    memcpy(&magic, p, 4);
+    memcpy(&ver, p + 4, 4);
+    memcpy(&np, p + 8, 8);
+    memcpy(&st, p + 16, 8);
+    if (magic != kNetMagic || ver != kNetVersion || np != N_PARAMS || st < 0) return RT_ERR_INVALID;
+    if (cudaMemcpyAsync(m->P, p + head, body, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(m->Mm, p + head + body, body, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(m->Vv, p + head + 2 * body, body, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return RT_ERR_CUDA;
+    refresh_bf16_kernel<<<512, 256, 0, s>>>(m->P, m->W1b, m->W2b, m->W2bT);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return RT_ERR_CUDA;
+    m->steps = st;
+    return RT_OK;
+}
+
+}  // namespace rt
 
 extern "C" {
 
@@ -416,8 +629,14 @@ rt_status rt_mlp_create(rt_mlp **out, void *cuda_stream)
     if (e == cudaSuccess) e = A(&m->dZ1T, (size_t)MAXB * D_H * 2);
     if (e == cudaSuccess) e = A(&m->T, (size_t)MAXB * D_OUT * 4);
     if (e == cudaSuccess) e = A(&m->Y, (size_t)MAXB * D_OUT * 4);
+    if (e == cudaSuccess) e = A(&m->Eo, (size_t)MAXB * D_OUT * 4);
+    if (e == cudaSuccess) e = A(&m->part, (size_t)kSplit1 * MAXB * D_H * 4);
     if (e == cudaSuccess) e = A(&m->loss, 4);
     if (e == cudaSuccess) e = A(&m->err, 4);
+    if (e == cudaSuccess) e = gemm_attr<EpiReluBias>();
+    if (e == cudaSuccess) e = gemm_attr<EpiMaskT>();
+    if (e == cudaSuccess) e = gemm_attr<EpiStore>();
+    if (e == cudaSuccess) e = gemm_attr<EpiPartial>();
     if (e != cudaSuccess) {
         rt_mlp_destroy(m);
         return e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA;
@@ -462,10 +681,9 @@ rt_status rt_mlp_forward(rt_mlp *m, const void *x_bf16, int32_t n, float *y)
 {
     if (!m || !x_bf16 || !y) return RT_ERR_INVALID;
     if (n < 1 || n > MAXB) return mfail(m, RT_ERR_INVALID, "n must be in 1..256");
-    const int Mb = n <= 128 ? 128 : 256;
-    rt_status s = load_batch(m, x_bf16, nullptr, n, Mb);
+    rt_status s = load_batch(m, x_bf16, nullptr, n);
     if (s != RT_OK) return s;
-    if ((s = fwd_bwd(m, Mb, n, false)) != RT_OK) return s;
+    MC(m, rt::mlp_forward_async(m, n, m->s));
     MC(m, cudaMemcpyAsync(y, m->Y, (size_t)n * D_OUT * 4, cudaMemcpyDefault, m->s));
     return check_err(m);
 }
@@ -474,9 +692,9 @@ rt_status rt_mlp_gradients(rt_mlp *m, const void *x_bf16, const float *t, int32_
 {
     if (!m || !x_bf16 || !t) return RT_ERR_INVALID;
     if (n < 1 || n > MAXB) return mfail(m, RT_ERR_INVALID, "n must be in 1..256");
-    rt_status s = load_batch(m, x_bf16, t, n, MAXB);
+    rt_status s = load_batch(m, x_bf16, t, n);
     if (s != RT_OK) return s;
-    if ((s = fwd_bwd(m, MAXB, n, true)) != RT_OK) return s;
+    MC(m, fwd_bwd(m, MAXB, n, true, m->loss, m->s));
     if (grads) MC(m, cudaMemcpyAsync(grads, m->G, N_PARAMS * 4, cudaMemcpyDefault, m->s));
     if (loss) MC(m, cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDefault, m->s));
     return check_err(m);
@@ -484,17 +702,14 @@ rt_status rt_mlp_gradients(rt_mlp *m, const void *x_bf16, const float *t, int32_
 
 rt_status rt_mlp_train_step(rt_mlp *m, const void *x_bf16, const float *t, int32_t n, double lr, float *loss)
 {
-    rt_status s = rt_mlp_gradients(m, x_bf16, t, n, nullptr, nullptr);
+    if (!m || !x_bf16 || !t) return RT_ERR_INVALID;
+    if (n < 1 || n > MAXB) return mfail(m, RT_ERR_INVALID, "n must be in 1..256");
+    rt_status s = load_batch(m, x_bf16, t, n);
     if (s != RT_OK) return s;
-    m->steps += 1;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.0f - powf(b1, (float)m->steps), c2 = 1.0f - powf(b2, (float)m->steps);
-    adam_kernel<<<1024, 256, 0, m->s>>>(m->P, m->G, m->Mm, m->Vv, (float)lr, b1, b2, 1e-8f, c1, c2, m->W1b, m->W2b,
-                                        m->W2bT);
-    MC(m, cudaGetLastError());
+    MC(m, fwd_bwd(m, MAXB, n, true, m->loss, m->s));
+    MC(m, adam(m, lr, m->s));
     if (loss) MC(m, cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDefault, m->s));
-    MC(m, cudaStreamSynchronize(m->s));
-    return RT_OK;
+    return check_err(m);
 }
 
 const char *rt_mlp_last_error(rt_mlp *m) { return m ? m->msg.c_str() : ""; }
@@ -535,7 +750,7 @@ void rt_mlp_destroy(rt_mlp *m)
     if (!m) return;
     if (m->s) cudaStreamSynchronize(m->s);
     void *ps[] = {m->P, m->G, m->Mm, m->Vv, m->W1b, m->W2b, m->W2bT, m->X, m->XT, m->H1, m->H1T, m->H2,
-                  m->dZ2, m->dZ2T, m->dZ1T, m->T, m->Y, m->loss, m->err};
+                  m->dZ2, m->dZ2T, m->dZ1T, m->T, m->Y, m->Eo, m->part, m->loss, m->err};
     for (void *p : ps)
         if (p) cudaFree(p);
     delete m;

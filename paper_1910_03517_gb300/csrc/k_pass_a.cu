@@ -70,6 +70,10 @@ __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const Pa
         for (size_t i = tid; i < a.clear_u32_n; i += nt) a.clear_u32[i] = 0u;
         for (size_t i = tid; i < a.clear_u64_n; i += nt) a.clear_u64[i] = 0ull;
     }
+    // surrogate mode: gate[0] = this frame set's band statistics are needed,
+    // gate[1] = the previous frame set's band luma is there for the motion test
+    if (a.gate && !a.gate[0]) return;
+    const bool first = a.first || (a.gate && !a.gate[1]);
     __syncthreads();
 
     const int upr = a.S / kUnitCols;
@@ -122,7 +126,7 @@ __global__ void __launch_bounds__(256) pass_a_kernel(const ArrayGeom g, const Pa
         const size_t lo = lbase + (size_t)y * a.S + (x0 - xb);
         *reinterpret_cast<uint4 *>(a.cur_luma + lo) = make_uint4(luma[0], luma[1], luma[2], luma[3]);
         uint32_t prev[4] = {luma[0], luma[1], luma[2], luma[3]};
-        if (!a.first) {
+        if (!first) {
             const uint4 P = ld16(a.prev_luma + lo);
             prev[0] = P.x; prev[1] = P.y; prev[2] = P.z; prev[3] = P.w;
         }

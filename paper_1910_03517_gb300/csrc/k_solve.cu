@@ -19,6 +19,7 @@
 #include <cstring>
 
 #include "rt_internal.cuh"
+#include "q16.cuh"
 #include "../../include/rt_check.h"
 
 namespace rt {
@@ -105,21 +106,6 @@ __device__ __forceinline__ double exp_table(double x, const SolveTables &t)
     return __hiloint2double(__double2hiint(y) + (k >> 6) * (1 << 20), __double2loint(y));
 }
 
-// round-half-away-from-zero of 65536 v for |v| < 2^15, from the bits of v
-// (no FP64 instruction)
-__device__ __forceinline__ int32_t q16_round(double v)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const int ex = (int)((b >> 52) & 2047) - 1023;
-    const unsigned long long mant = (b & ((1ull << 52) - 1)) | (1ull << 52);
-    const int sh = 36 - ex;                       // 65536 |v| = mant 2^-sh
-    int32_t q;
-    if (sh >= 64) q = 0;
-    else if (sh <= 0) q = (int32_t)(mant << -sh);
-    else q = (int32_t)((mant + (1ull << (sh - 1))) >> sh);
-    return (b >> 63) ? -q : q;
-}
-
 // One system (chain, block, channel) per CTA of one warp, one camera of the
 // chain per lane; the systems of a frame set spread over SMs.
 //
@@ -142,6 +128,7 @@ __global__ void __launch_bounds__(32) solve_global_kernel(const SolveArgs a)
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x;
     const int sys = blockIdx.x;
+    if (a.gate && !a.gate[0]) return;                 // surrogate mode: no fit for this frame set
     const int c = sys % 3, j = (sys / 3) % a.B, grp = sys / (3 * a.B);
     const int g0 = a.topo.gstart[grp];
     const int n = a.topo.gstart[grp + 1] - g0;
@@ -263,6 +250,11 @@ __global__ void __launch_bounds__(32) solve_global_kernel(const SolveArgs a)
     gb = max(gb, __double_as_longlong(a.gmin));
     gb = min(gb, __double_as_longlong(a.gmax));
     const double g = __longlong_as_double(gb);
+    const double2 m = make_double2(g, 0.0);
+    // both sides carry the same gain
+    *reinterpret_cast<double2 *>(a.maps_new + i0) = m;
+    *reinterpret_cast<double2 *>(a.maps_new + i1) = m;
+    if (a.fit_only) return;                           // smoothing and Q16 left to the caller
     double2 e;
     if (a.first) {
         e = make_double2(g, 0.0);
@@ -271,10 +263,6 @@ __global__ void __launch_bounds__(32) solve_global_kernel(const SolveArgs a)
         e.y = a.one_m_alpha * e_old.y;
     }
     const int2 q = make_int2(q16_round(e.x), q16_round(e.y));
-    const double2 m = make_double2(g, 0.0);
-    // both sides carry the same gain
-    *reinterpret_cast<double2 *>(a.maps_new + i0) = m;
-    *reinterpret_cast<double2 *>(a.maps_new + i1) = m;
     *reinterpret_cast<double2 *>(a.E + i0) = e;
     *reinterpret_cast<double2 *>(a.E + i1) = e;
     *reinterpret_cast<int2 *>(a.q16 + i0) = q;

@@ -28,170 +28,17 @@
 
 using namespace rt;
 
-namespace {
+#include "rt_handle.cuh"
 
-constexpr int kEvRing = 4;
-constexpr int kQRing = 3;
-#ifndef RT_STRIP_ROWS
-#define RT_STRIP_ROWS 64
-#endif
-constexpr int kStripRows = RT_STRIP_ROWS;   // rows of one pass-A work item
-constexpr uint32_t kStateMagic = 0x52545331u;
-constexpr int kMaxProfiled = 4096;  // frame sets whose pass times one collection keeps
-
-// CUDA events around the passes of one frame set (profiling)
-struct ProfEv {
-    cudaEvent_t a0, a1, s0, s1, b0, b1, c1;
-    bool crops, all;
-};
-
+namespace rt {
+namespace host {
 thread_local std::string g_config_error;
+}  // namespace host
+}  // namespace rt
 
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-}  // namespace
-
-struct rt_handle {
-    rt_array_params p{};
-    std::vector<rt_camera_desc> cams;
-    int dev = 0, sm_count = 0;
-    cudaStream_t user = nullptr, s_stats = nullptr, s_solve = nullptr, s_main = nullptr, s_copy = nullptr,
-                 s_d2h = nullptr;
-    cudaStream_t s_prof[3] = {nullptr, nullptr, nullptr};   // timing branches of s_stats, s_solve, s_main
-    ArrayGeom geom{};
-    int Hmax = 0;
-    // outputs and statistics
-    uint8_t *rgb[2] = {nullptr, nullptr};
-    std::vector<size_t> rgb_off;
-    size_t rgb_bytes = 0;
-    uint32_t *frame_hist[2] = {nullptr, nullptr};
-    uint32_t *thumbs[2] = {nullptr, nullptr};
-    uint32_t *strip_hist[3] = {nullptr, nullptr, nullptr};
-    uint32_t *strip_n[3] = {nullptr, nullptr, nullptr};
-    unsigned long long *strip_sum[3] = {nullptr, nullptr, nullptr}, *strip_sumsq[3] = {nullptr, nullptr, nullptr};
-    unsigned long long *strip_joint[3] = {nullptr, nullptr, nullptr};   // [K][2][B][10] (3 x 3 maps)
-    uint8_t *luma[2] = {nullptr, nullptr};
-    size_t luma_cam_stride = 0;
-    double *maps_new = nullptr, *E = nullptr;
-    int32_t *q16[kQRing] = {nullptr, nullptr, nullptr};
-    int32_t *q16_identity = nullptr;
-    int32_t *ramp = nullptr;
-    StripItem *items = nullptr;
-    int n_items = 0;
-    int32_t *group_start = nullptr, *group_members = nullptr, *left_nbr = nullptr, *right_nbr = nullptr,
-            *cam_H = nullptr;
-    int n_groups = 0;
-    SolveTopo solve_topo{};
-    // seams (left camera, right camera) in chain order, and their costs
-    std::vector<int2> seam_list;
-    int2 *seams = nullptr;
-    double *seam_cost[2] = {nullptr, nullptr};
-    double *seam_rows = nullptr;   // per averaged row terms [seams][seam_max_rows]
-    int seam_max_rows = 0;
-    // difference attention
-    AttnArgs attn{};
-    uint8_t *luma_copy[2] = {nullptr, nullptr};
-    uint32_t *attn_cells = nullptr;
-    rt_crop *props[2] = {nullptr, nullptr};
-    int32_t *prop_count[2] = {nullptr, nullptr};
-    cudaStream_t s_attn = nullptr, s_aux = nullptr;   // attention; seam costs
-    cudaEvent_t ev_attn[4] = {}, ev_pb[4] = {}, ev_seam[4] = {};
-    bool crops_from_props[2] = {false, false};
-    bool attn_valid = false;       // luma_copy of the previous frame set holds its luma
-    int32_t *q16_rows[2] = {nullptr, nullptr};   // per-row blended maps [K][2][Hmax][3][2]
-    __half *crops[2] = {nullptr, nullptr};
-    rt_crop *crop_dev[2] = {nullptr, nullptr};
-    rt_crop *crop_host = nullptr;          // pinned [2][max_crops]
-    int n_crops[2] = {0, 0};
-    // host-input staging
-    uint8_t *stage[2] = {nullptr, nullptr};
-    std::vector<size_t> stage_y_off, stage_uv_off;
-    size_t stage_bytes = 0;
-    // events
-    cudaEvent_t ev_user = nullptr, ev_in = nullptr, ev_tmp = nullptr;
-    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;   // autotuner timing
-    cudaEvent_t ev_a[kEvRing] = {}, ev_solved[kEvRing] = {}, ev_done[kEvRing] = {}, ev_out[kEvRing] = {};
-    bool launched[kEvRing] = {}, out_launched[kEvRing] = {};
-    int64_t t = 0;                 // frame sets submitted
-    bool restart = true;           // next submit starts a sequence
-    bool last_first = true;        // the last frame set started its sequence
-    // profiling
-    bool prof_on = false, prof_all = true;
-    std::vector<ProfEv> prof, cap_prof;
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_pool_used = 0;
-    bool last_was_graph = false;
-    bool graph_launched = false;   // the captured graph ran since profiling started
-    // captured sequence
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
-    int cap_n = 0;
-    int64_t cap_t0 = 0;
-    bool capturing = false;
-    rt_crop *cap_crops = nullptr;
-    size_t cap_crops_n = 0;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_mark = nullptr;
-    bool prof_branch[3] = {false, false, false};   // the capture in progress used s_prof[i]
-    // launch shapes (rt_autotune / rt_set_tuning)
-    int pb_grid = 0, pb_threads = RT_PASS_B_RUN_THREADS, pb_ctas = RT_PASS_B_CTAS_PER_SM;
-    int pa_rows = kStripRows, pa_threads = 128, crop_threads = 256, crop_grid = 64;
-    rt_tuning tuned{};
-    size_t pb_smem = 0;
-    std::string err;
-    size_t n_maps = 0;             // K*2*B*6, or K*2*B*12 for the 3 x 3 maps
-    // surrogate inference buffers (allocated on first use)
-    void *sg_x = nullptr;          // BF16 [K][6912]
-    float *sg_y = nullptr;         // [K][3]
-    double *sg_maps = nullptr, *sg_err = nullptr;
-};
+using namespace rt::host;
 
 namespace {
-
-rt_status fail(rt_handle *h, rt_status s, const std::string &msg)
-{
-    if (h) h->err = msg;
-    else g_config_error = msg;
-    return s;
-}
-
-rt_status cuda_fail(rt_handle *h, cudaError_t e, const char *what)
-{
-    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
-    return fail(h, e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, m);
-}
-
-#define RT_CUDA(h, call)                                   \
-    do {                                                   \
-        cudaError_t e_ = (call);                           \
-        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
-    } while (0)
-
-rt_status wait_event(rt_handle *h, cudaEvent_t ev, int32_t timeout_ms)
-{
-    auto t0 = std::chrono::steady_clock::now();
-    for (;;) {
-        cudaError_t e = cudaEventQuery(ev);
-        if (e == cudaSuccess) return RT_OK;
-        if (e != cudaErrorNotReady) return cuda_fail(h, e, "cudaEventQuery");
-        if (timeout_ms >= 0) {
-            auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
-            if (ms >= timeout_ms) return fail(h, RT_ERR_TIMEOUT, "timed out waiting for the GPU");
-        }
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
-    }
-}
-
-template <class T>
-rt_status dalloc(rt_handle *h, T **p, size_t n)
-{
-    *p = nullptr;
-    if (n == 0) return RT_OK;
-    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
-    e = cudaMemset(*p, 0, n * sizeof(T));
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset");
-    return RT_OK;
-}
 
 // Band-statistics work items: (camera, side, block) rows split into chunks
 // of h->pa_rows rows (the device table is rebuilt when the shape changes).
@@ -296,6 +143,16 @@ rt_status validate(const rt_array_params *p)
             return fail(nullptr, RT_ERR_INVALID, "attn_window must be a multiple of 32 in 32..4096");
         if (p->attn_min_on < 1) return fail(nullptr, RT_ERR_INVALID, "attn_min_on must be >= 1");
         if (p->attn_max < 1 || p->attn_max > 4096) return fail(nullptr, RT_ERR_INVALID, "attn_max must be in 1..4096");
+    }
+    if (p->surrogate_mode != 0 && p->surrogate_mode != 1)
+        return fail(nullptr, RT_ERR_INVALID, "surrogate_mode must be 0 or 1");
+    if (p->surrogate_mode) {
+        if (p->fit_mode != RT_FIT_GLOBAL || p->num_blocks != 1 || !(p->flags & RT_FLAG_THUMBNAILS) ||
+            p->schedule != RT_SCHED_CURRENT)
+            return fail(nullptr, RT_ERR_INVALID,
+                        "surrogate mode needs per-camera gains, one block, RT_FLAG_THUMBNAILS and the current schedule");
+        if (p->judge_every < 1) return fail(nullptr, RT_ERR_INVALID, "judge_every must be >= 1");
+        if (!(p->fallback_tol >= 0.0)) return fail(nullptr, RT_ERR_INVALID, "fallback_tol must be >= 0");
     }
     if (p->flags & RT_FLAG_SEAM_COST)
         for (int k = 0; k < p->num_cameras; ++k)
@@ -620,6 +477,13 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     const int par = (int)(t & 1), ev = (int)(t % kEvRing), qs = (int)(t % kQRing);
     const int ss = (int)(t % 3), ss_next = (int)((t + 1) % 3);   // band-statistics slots
     const bool first = h->restart || frame_index == 0;
+    if (p.surrogate_mode) {
+        if (h->capturing && !(h->sg && surrogate_net(h))) return fail(h, RT_ERR_STATE, "no surrogate network");
+        if (!h->capturing) {
+            rt_status s = surrogate_ready(h);
+            if (s != RT_OK) return s;
+        }
+    }
 
     ArrayGeom g = h->geom;
     for (int k = 0; k < K; ++k) {
@@ -679,6 +543,16 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
         pe.all = prof_chain;
         if (prof_chain) RT_CUDA(h, prof_record(h, pe.a0, h->s_stats));
     }
+    // surrogate mode: the prediction from the previous frame set's thumbnails
+    // (pass B(t-1) done first) and the device-side decision whether the fit runs
+    const bool sur = p.surrogate_mode != 0;
+    if (sur) {
+        const int evp = (int)((t + kEvRing - 1) % kEvRing);
+        const bool dep1 = h->capturing ? (t - 1 >= h->cap_t0) : (t >= 1 && h->launched[evp]);
+        if (!first && dep1) RT_CUDA(h, cudaStreamWaitEvent(h->s_stats, h->ev_done[evp], 0));
+        rt_status s = surrogate_predict_step(h, h->thumbs[par ^ 1], first);
+        if (s != RT_OK) return s;
+    }
     // statistics chain: pass A -> solve
     PassAArgs pa{};
     pa.items = h->items; pa.n_items = h->n_items; pa.S = p.strip_width; pa.T = p.motion_threshold;
@@ -690,6 +564,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     pa.clear_u32 = h->strip_hist[ss_next]; pa.clear_u32_n = nb * 768 + nb * 3;
     pa.joint = h->strip_joint[ss];
     pa.clear_u64 = h->strip_sum[ss_next]; pa.clear_u64_n = nb * 3 * 2 + (pa.joint ? nb * 10 : 0);
+    pa.gate = sur ? surrogate_gate(h) : nullptr;
     RT_CUDA(h, launch_pass_a(g, pa, h->pa_threads, h->s_stats));
     if (prof_chain) RT_CUDA(h, prof_record(h, pe.a1, h->s_stats));
     RT_CUDA(h, cudaEventRecord(h->ev_a[ev], h->s_stats));
@@ -704,8 +579,14 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     sa.n_groups = h->n_groups; sa.group_start = h->group_start; sa.group_members = h->group_members;
     sa.left_nbr = h->left_nbr; sa.right_nbr = h->right_nbr; sa.cam_H = h->cam_H;
     sa.topo = h->solve_topo;
+    sa.gate = sur ? surrogate_gate(h) : nullptr;
+    sa.fit_only = sur ? 1 : 0;
     if (prof_chain) RT_CUDA(h, prof_record(h, pe.s0, h->s_solve));
     RT_CUDA(h, launch_solve(sa, h->s_solve));
+    if (sur) {
+        rt_status s = surrogate_select_step(h, h->q16[qs], first);
+        if (s != RT_OK) return s;
+    }
     if (prof_chain) RT_CUDA(h, prof_record(h, pe.s1, h->s_solve));
     RT_CUDA(h, cudaEventRecord(h->ev_solved[ev], h->s_solve));
 
@@ -849,6 +730,9 @@ void rt_default_params(rt_array_params *p)
     p->attn_window = 256;
     p->attn_min_on = 655;
     p->attn_max = 256;
+    p->surrogate_mode = 0;
+    p->judge_every = 8;
+    p->fallback_tol = 0.02;
 }
 
 rt_status rt_array_config(const rt_array_params *params, void *cuda_stream, rt_handle **out)
@@ -1089,7 +973,9 @@ rt_status rt_get_thumb_features(rt_handle *h, void *x_bf16, int32_t timeout_ms)
 
 rt_status rt_surrogate_predict(rt_handle *h, rt_mlp *m, double *maps_fp64, double *max_error, int32_t timeout_ms)
 {
-    if (!h || !m) return RT_ERR_INVALID;
+    if (!h) return RT_ERR_INVALID;
+    if (!m) m = surrogate_net(h);
+    if (!m) return fail(h, RT_ERR_STATE, "no surrogate network (rt_surrogate_train or rt_surrogate_load)");
     const int K = h->p.num_cameras;
     if (h->p.fit_mode != RT_FIT_GLOBAL || h->p.num_blocks != 1 || !(h->p.flags & RT_FLAG_THUMBNAILS))
         return fail(h, RT_ERR_STATE, "the surrogate needs per-camera gains, one block and RT_FLAG_THUMBNAILS");
@@ -1525,7 +1411,7 @@ rt_status rt_autotune(rt_handle *h, int32_t n_sets, const void *const *y_planes,
     if (s == RT_OK) {
         const rt_tuning base = best;
         for (int ctas = 1; ctas <= 2 && s == RT_OK; ++ctas)
-            for (int thr : {256, 320, 384, 448, 512}) {
+            for (int thr : {256, 320, 352, 384, 448, 512}) {
                 rt_tuning c = base;
                 c.pass_b_ctas_per_sm = ctas;
                 c.pass_b_threads = thr;
@@ -1638,7 +1524,7 @@ rt_status rt_save_state(rt_handle *h, void *buf, size_t *len)
 {
     if (!h || !len) return RT_ERR_INVALID;
     const size_t luma_bytes = (size_t)h->p.num_cameras * h->luma_cam_stride;
-    const size_t need = 4 * sizeof(uint32_t) + sizeof(int64_t) + h->n_maps * 8 + luma_bytes;
+    const size_t need = 4 * sizeof(uint32_t) + sizeof(int64_t) + h->n_maps * 8 + luma_bytes + surrogate_state_bytes(h);
     if (!buf) { *len = need; return RT_OK; }
     if (*len < need) { *len = need; return fail(h, RT_ERR_INVALID, "buffer too small"); }
     rt_status s = rt_sync(h, -1);
@@ -1654,6 +1540,8 @@ rt_status rt_save_state(rt_handle *h, void *buf, size_t *len)
     b += h->n_maps * 8;
     if (h->t > 0) RT_CUDA(h, cudaMemcpy(b, h->luma[(int)((h->t - 1) & 1)], luma_bytes, cudaMemcpyDeviceToHost));
     else memset(b, 0, luma_bytes);
+    b += luma_bytes;
+    if ((s = surrogate_state_save(h, b)) != RT_OK) return s;   // surrogate mode: fallback, judge cadence
     *len = need;
     return RT_OK;
 }
@@ -1662,7 +1550,7 @@ rt_status rt_load_state(rt_handle *h, const void *buf, size_t len)
 {
     if (!h || !buf) return RT_ERR_INVALID;
     const size_t luma_bytes = (size_t)h->p.num_cameras * h->luma_cam_stride;
-    const size_t need = 4 * sizeof(uint32_t) + sizeof(int64_t) + h->n_maps * 8 + luma_bytes;
+    const size_t need = 4 * sizeof(uint32_t) + sizeof(int64_t) + h->n_maps * 8 + luma_bytes + surrogate_state_bytes(h);
     if (len != need) return fail(h, RT_ERR_INVALID, "state blob of another configuration");
     const uint8_t *b = static_cast<const uint8_t *>(buf);
     uint32_t hdr[4];
@@ -1680,6 +1568,8 @@ rt_status rt_load_state(rt_handle *h, const void *buf, size_t len)
     // the next frame set compares its band luma with the saved one
     const int par_prev = (int)((h->t + 1) & 1);
     RT_CUDA(h, cudaMemcpy(h->luma[par_prev], b, luma_bytes, cudaMemcpyHostToDevice));
+    b += luma_bytes;
+    if ((s = surrogate_state_load(h, b)) != RT_OK) return s;
     h->restart = hdr[3] != 0;
     h->attn_valid = false;     // the attention's full-frame luma is not part of the state
     (void)t;
@@ -1695,6 +1585,7 @@ void rt_destroy(rt_handle *h)
 {
     if (!h) return;
     rt_sync(h, 10000);
+    surrogate_free(h);
     free_all(h);
     delete h;
 }

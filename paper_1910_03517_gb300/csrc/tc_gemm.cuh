@@ -137,11 +137,12 @@ struct Smem {
     static constexpr int kBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 };
 
-// The GEMM mainloop + epilogue.  Epi is called per thread with
+// The GEMM mainloop + epilogue over the K range [k0, k0 + K) (a split of a
+// longer contraction when k0 > 0).  Epi is called per thread with
 // (row, col0, 32 FP32 values of columns col0..col0+31).
 template <int BN, class Epi>
-__device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensorMap *tmB, int K, const Epi &epi,
-                                          int *err)
+__device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensorMap *tmB, int k0, int K,
+                                          const Epi &epi, int *err)
 {
     static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "BN");
     extern __shared__ uint8_t smem_raw[];
@@ -192,8 +193,8 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
             uint8_t *a = tiles + s * Smem<BN>::kStageBytes;
             uint8_t *b = a + Smem<BN>::kABytes;
             mbar_expect_tx(&full[s], Smem<BN>::kStageBytes);
-            tma_load_2d(a, tmA, &full[s], kb * kBK, m0);
-            tma_load_2d(b, tmB, &full[s], kb * kBK, n0);
+            tma_load_2d(a, tmA, &full[s], k0 + kb * kBK, m0);
+            tma_load_2d(b, tmB, &full[s], k0 + kb * kBK, n0);
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer

@@ -52,7 +52,17 @@ class ArrayParams(ctypes.Structure):
                 ("motion_threshold", c_i32), ("min_valid", c_i32), ("color_matrix", c_i32),
                 ("alpha", c_dbl), ("lambda_", c_dbl), ("gain_min", c_dbl), ("gain_max", c_dbl),
                 ("max_crops", c_i32), ("crop_size", c_i32), ("flags", c_i32),
-                ("attn_window", c_i32), ("attn_min_on", c_i32), ("attn_max", c_i32)]
+                ("attn_window", c_i32), ("attn_min_on", c_i32), ("attn_max", c_i32),
+                ("surrogate_mode", c_i32), ("judge_every", c_i32), ("fallback_tol", c_dbl)]
+
+
+class SurrogateReport(ctypes.Structure):
+    _fields_ = [("frame_sets", c_i64), ("predicted", c_i64), ("plain", c_i64), ("judged", c_i64),
+                ("judged_failed", c_i64), ("fallback", c_i32), ("last_error", c_dbl), ("max_error", c_dbl),
+                ("tolerance", c_dbl)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 class Crop(ctypes.Structure):
@@ -477,14 +487,62 @@ class CameraArray:
         return {"frame_sets": r.frame_sets, "pass_a_ms": r.pass_a_ms, "solve_ms": r.solve_ms,
                 "pass_b_ms": r.pass_b_ms, "crops_ms": r.crops_ms}
 
-    def surrogate_predict(self, net: "GainMLP", timeout_ms: int = 60000):
-        """(maps [K,2,1,3,2] predicted by the network, judge error vs the fit)."""
+    def surrogate_predict(self, net: Optional["GainMLP"] = None, timeout_ms: int = 60000):
+        """(maps [K,2,1,3,2] predicted by the network -- net, or the handle's
+        own when None -- and the judge's error against the fit)."""
         _load_mlp(self.L)
         maps = np.zeros((self.K, 2, self.B, 3, 2), np.float64)
         err = np.zeros(1, np.float64)
-        _check(self.L, self.h, self.L.rt_surrogate_predict(self.h, net.h, maps.ctypes.data, err.ctypes.data,
-                                                           timeout_ms))
+        _check(self.L, self.h, self.L.rt_surrogate_predict(self.h, net.h if net is not None else None,
+                                                           maps.ctypes.data, err.ctypes.data, timeout_ms))
         return maps, float(err[0])
+
+    # -- the array's own surrogate network (rt_surrogate.h) ---------------
+    def surrogate_train(self, n_samples: int, batch: int = 256, lr: float = 1e-3, seed: int = 0):
+        """One pass of training over n_samples generated samples; returns the step losses."""
+        _load_mlp(self.L)
+        _check(self.L, self.h, self.L.rt_surrogate_train(self.h, int(n_samples), int(batch), float(lr), int(seed)))
+        n = c_i64(0)
+        _check(self.L, self.h, self.L.rt_surrogate_losses(self.h, None, 0, ctypes.byref(n)))
+        out = np.zeros(max(1, n.value), np.float32)
+        _check(self.L, self.h, self.L.rt_surrogate_losses(self.h, out.ctypes.data, n.value, ctypes.byref(n)))
+        return out[: n.value]
+
+    def surrogate_evaluate(self, n_samples: int, seed: int):
+        """Per-camera held-out gain error [sets, K] of the handle's network, and
+        the same error of leaving the cameras uncorrected."""
+        _load_mlp(self.L)
+        n = c_i64(0)
+        cap = -(-int(n_samples) // self.K) * self.K
+        out = np.zeros(cap, np.float64)
+        out0 = np.zeros(cap, np.float64)
+        _check(self.L, self.h, self.L.rt_surrogate_evaluate(self.h, int(n_samples), int(seed), out.ctypes.data,
+                                                             out0.ctypes.data, cap, ctypes.byref(n)))
+        return out[: n.value].reshape(-1, self.K), out0[: n.value].reshape(-1, self.K)
+
+    def surrogate_save(self, path: str):
+        _load_mlp(self.L)
+        _check(self.L, self.h, self.L.rt_surrogate_save(self.h, path.encode()))
+
+    def surrogate_load(self, path: str):
+        _load_mlp(self.L)
+        _check(self.L, self.h, self.L.rt_surrogate_load(self.h, path.encode()))
+
+    def surrogate_params(self) -> np.ndarray:
+        _load_mlp(self.L)
+        a = np.zeros(MLP_PARAMS, np.float32)
+        _check(self.L, self.h, self.L.rt_surrogate_get_params(self.h, a.ctypes.data, a.size))
+        return a
+
+    def surrogate_set_tolerance(self, tol: float):
+        _load_mlp(self.L)
+        _check(self.L, self.h, self.L.rt_surrogate_set_tolerance(self.h, float(tol)))
+
+    def surrogate_report(self, timeout_ms: int = 60000) -> Dict[str, float]:
+        _load_mlp(self.L)
+        r = SurrogateReport()
+        _check(self.L, self.h, self.L.rt_surrogate_get_report(self.h, ctypes.byref(r), timeout_ms))
+        return r.as_dict()
 
     def thumb_features(self, timeout_ms: int = 60000):
         """BF16 device tensor [K, 6912] of the last frame set's thumbnail features."""
@@ -526,7 +584,9 @@ class CameraArray:
 MLP_INPUTS = 6912
 MLP_PARAMS = 1836291
 MLP_EXPORTS = ["rt_mlp_create", "rt_mlp_set_params", "rt_mlp_get_params", "rt_mlp_forward", "rt_mlp_gradients",
-               "rt_mlp_train_step", "rt_mlp_last_error", "rt_mlp_destroy", "rt_surrogate_predict"]
+               "rt_mlp_train_step", "rt_mlp_last_error", "rt_mlp_destroy", "rt_surrogate_predict",
+               "rt_surrogate_train", "rt_surrogate_losses", "rt_surrogate_evaluate", "rt_surrogate_save",
+               "rt_surrogate_load", "rt_surrogate_get_params", "rt_surrogate_set_tolerance", "rt_surrogate_get_report"]
 
 
 def _load_mlp(L):
@@ -543,6 +603,18 @@ def _load_mlp(L):
     L.rt_mlp_destroy.argtypes = [c_vp]
     L.rt_mlp_destroy.restype = None
     L.rt_mlp_check_activations.argtypes = [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]
+    L.rt_surrogate_train.argtypes = [c_vp, c_i64, c_i32, c_dbl, ctypes.c_uint64]
+    L.rt_surrogate_losses.argtypes = [c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]
+    L.rt_surrogate_evaluate.argtypes = [c_vp, c_i64, ctypes.c_uint64, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]
+    L.rt_surrogate_save.argtypes = [c_vp, ctypes.c_char_p]
+    L.rt_surrogate_load.argtypes = [c_vp, ctypes.c_char_p]
+    L.rt_surrogate_get_params.argtypes = [c_vp, c_vp, c_sz]
+    L.rt_surrogate_set_tolerance.argtypes = [c_vp, c_dbl]
+    L.rt_surrogate_get_report.argtypes = [c_vp, ctypes.POINTER(SurrogateReport), c_i32]
+    for name in MLP_EXPORTS:
+        fn = getattr(L, name)
+        if fn.restype is ctypes.c_int:
+            fn.restype = c_i32
     L.rt_surrogate_predict.argtypes = [c_vp, c_vp, c_vp, c_vp, c_i32]
     L.rt_surrogate_predict.restype = c_i32
     for n in MLP_EXPORTS[:-3]:

@@ -7,7 +7,8 @@ memory in a fixed array inside the library.  Checked here: two calls in a
 row on different frame sets give the maps of the handle path's first frame
 set within the tolerance the parity tests use (1e-6 relative for FP64
 maps, exact Q16), so the second call is not disturbed by what the first
-left in the shared array.  This file is collected last on purpose.
+left in the shared array, and the second call leaves the device's free
+memory unchanged.  This file is collected last on purpose.
 """
 import ctypes
 
@@ -45,10 +46,15 @@ def test_noalloc_matches_handle_path_twice():
         uv = (ctypes.c_void_p * K)(*[(f["uv"].data_ptr() if "uv" in f else None) for f in fs])
         maps = torch.full((K, 2, B, 3, 2), -7.0, dtype=torch.float64, device="cuda")
         q16 = torch.full((K, 2, B, 3, 2), -7, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         st = L.rt_fit_gains_noalloc(descs, K, y, uv, 32, B, rt.RT_RING, maps.data_ptr(), q16.data_ptr(),
                                     ctypes.c_void_p(stream.cuda_stream))
         assert st == rt.RT_OK
         torch.cuda.synchronize()
+        if t == 1:
+            # the second call takes no device memory (the first may load the module)
+            assert torch.cuda.mem_get_info()[0] == free0
         m = maps.cpu().numpy()
         q = q16.cpu().numpy()
         assert (np.abs(m - m_ref) <= 1e-6 * np.abs(m_ref) + 1e-9).all(), (t, np.abs(m - m_ref).max())
