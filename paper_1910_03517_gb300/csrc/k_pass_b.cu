@@ -133,16 +133,19 @@ __device__ __forceinline__ uint32_t clamp_hi2(uint32_t t0, uint32_t t1)
     return r;
 }
 
+// The same for signed t (seam maps can give negative values): the high
+// halves as signed 16-bit floor(t / 65536), clamped to [0, 255] by one packed
+// min with ReLU.
+__device__ __forceinline__ uint32_t clamp_hi2s(uint32_t t0, uint32_t t1)
+{
+    const uint32_t hi = __byte_perm(t0, t1, 0x7632u);
+    uint32_t r;
+    asm("min.relu.s16x2 %0, %1, %2;" : "=r"(r) : "r"(hi), "r"(0x00FF00FFu));
+    return r;
+}
+
 // Bytes 0 and 2 of a and of b: [a.0, a.2, b.0, b.2].
 __device__ __forceinline__ uint32_t even_bytes(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x6420u); }
-
-// Pack byte 2 of four values into one word (t0 lowest): three PRMTs.
-__device__ __forceinline__ uint32_t pack4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3)
-{
-    const uint32_t lo = __byte_perm(t0, t1, 0x0062u);   // [t0.2, t1.2, -, -]
-    const uint32_t hi = __byte_perm(t2, t3, 0x6200u);   // [-, -, t2.2, t3.2]
-    return __byte_perm(lo, hi, 0x7610u);
-}
 
 __device__ __forceinline__ RowGain row_gain(const int32_t *__restrict__ q16, int cam, int j, int B)
 {
@@ -207,12 +210,6 @@ __device__ __forceinline__ void load_map(const int32_t *__restrict__ q16, int ca
     load_map12(q16, cam, side, j, B, m);
 }
 
-__device__ __forceinline__ uint32_t clamp24(uint32_t t)
-{
-    const int v = (int)t;
-    return (uint32_t)(v < 0 ? 0 : (v > 0xFFFFFF ? 0xFFFFFF : v));
-}
-
 // Column coefficients of a map: NV = 6 (affine: A_c, cst_c) or 12 (3 x 3:
 // A_cd row-major, cst_c).  w14 = 16384 w.
 template <int NV> struct ColCoef;
@@ -246,18 +243,25 @@ __device__ __forceinline__ void col_coef(const int (&m)[12], int w14, ColCoef<12
     }
 }
 
-// Output words (byte 2 = the 8-bit result) of one pixel's three value bits.
+// t = 65536 x (the unclamped result, as a signed 32-bit value) + low bits
+// of one pixel's three value bits; clamp_hi2s turns pairs into bytes.
 __device__ __forceinline__ void col_apply(const ColCoef<6> &k, const uint32_t (&vb)[3], uint32_t *t)
 {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) t[c] = clamp24(k.A[c] * vb[c] + k.cst[c]);
+    for (int c = 0; c < 3; ++c) t[c] = k.A[c] * vb[c] + k.cst[c];
 }
 
 __device__ __forceinline__ void col_apply(const ColCoef<12> &k, const uint32_t (&vb)[3], uint32_t *t)
 {
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-        t[c] = clamp24(k.A[3 * c] * vb[0] + k.A[3 * c + 1] * vb[1] + k.A[3 * c + 2] * vb[2] + k.cst[c]);
+    for (int c = 0; c < 3; ++c) t[c] = k.A[3 * c] * vb[0] + k.A[3 * c + 1] * vb[1] + k.A[3 * c + 2] * vb[2] + k.cst[c];
+}
+
+// Output byte 2 of a seam-map value t, clamped (mono cameras, one value at a time).
+__device__ __forceinline__ uint32_t clamp24(uint32_t t)
+{
+    const int v = (int)t;
+    return (uint32_t)(v < 0 ? 0 : (v > 0xFFFFFF ? 0xFFFFFF : v));
 }
 
 // Thumbnail cell sums of one row's 16 converted pixels (vbits vb[i][c]):
@@ -377,12 +381,12 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
             for (int r = 0; r < 2; ++r)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {             // pixels 2h, 2h+1 share a chroma pair
-                    const float Y0f = byte_f(yw[r][g4], 2 * h), Y1f = byte_f(yw[r][g4], 2 * h + 1);
+                    const F2 Yf = bytes_f2(yw[r][g4], 2 * h, 2 * h + 1);
                     float z0[3], z1[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        z0[c] = __saturatef(fmaf(Y0f, k.ky, cz[h][c]));
-                        z1[c] = __saturatef(fmaf(Y1f, k.ky, cz[h][c]));
+                        z0[c] = __saturatef(fmaf(Yf.x, k.ky, cz[h][c]));
+                        z1[c] = __saturatef(fmaf(Yf.y, k.ky, cz[h][c]));
                     }
                     magic2(z0[0], z0[1], vbq[r][2 * h][0], vbq[r][2 * h][1]);
                     magic2(z1[0], z1[1], vbq[r][2 * h + 1][0], vbq[r][2 * h + 1][1]);
@@ -428,9 +432,9 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
             }
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                ow[r][3 * g4 + 0] = pack4(t[r][0], t[r][1], t[r][2], t[r][3]);
-                ow[r][3 * g4 + 1] = pack4(t[r][4], t[r][5], t[r][6], t[r][7]);
-                ow[r][3 * g4 + 2] = pack4(t[r][8], t[r][9], t[r][10], t[r][11]);
+                ow[r][3 * g4 + 0] = even_bytes(clamp_hi2s(t[r][0], t[r][1]), clamp_hi2s(t[r][2], t[r][3]));
+                ow[r][3 * g4 + 1] = even_bytes(clamp_hi2s(t[r][4], t[r][5]), clamp_hi2s(t[r][6], t[r][7]));
+                ow[r][3 * g4 + 2] = even_bytes(clamp_hi2s(t[r][8], t[r][9]), clamp_hi2s(t[r][10], t[r][11]));
             }
         }
     }
@@ -495,7 +499,7 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
                 for (int c = 0; c < 3; ++c) {
                     if (STATS) hist_inc(hbase + vb * 128u, c);
                     const int bb = 3 * i + c;
-                    ow[r][bb >> 2] = put_byte2(ow[r][bb >> 2], t3[c], bb & 3);
+                    ow[r][bb >> 2] = put_byte2(ow[r][bb >> 2], clamp24(t3[c]), bb & 3);
                 }
             } else {
 #pragma unroll
