@@ -42,6 +42,17 @@ def test_defaults(L):
     p = rt.default_params()
     assert (p.strip_width, p.num_blocks, p.motion_threshold, p.min_valid) == (32, 1, 24, 64)
     assert p.alpha == 0.05 and p.lambda_ == 1e-6 and (p.gain_min, p.gain_max) == (0.25, 4.0)
+    assert (p.surrogate_mode, p.judge_every, p.fallback_tol) == (0, 8, 0.02)
+
+
+def test_surrogate_calls_refuse_a_null_handle(L):
+    from paper_1910_03517_gb300 import rt
+    rt._load_mlp(L)
+    assert L.rt_surrogate_train(None, 256, 256, 1e-3, 0) == rt.RT_ERR_INVALID
+    assert L.rt_surrogate_save(None, b"x") == rt.RT_ERR_INVALID
+    assert L.rt_surrogate_load(None, b"x") == rt.RT_ERR_INVALID
+    assert L.rt_surrogate_set_tolerance(None, 0.0) == rt.RT_ERR_INVALID
+    assert L.rt_surrogate_evaluate(None, 16, 0, None, None, 0, None) == rt.RT_ERR_INVALID
 
 
 def _config(L, cams, **kw):
@@ -70,6 +81,12 @@ def _config(L, cams, **kw):
     ((640, 480, 0, 8, 640, 640, 0, 0), {"fit_mode": 4}, "fit_mode"),
     ((640, 480, 0, 8, 640, 640, 0, 0), {"gain_max": 17.0}, "gain_max"),
     ((640, 480, 0, 8, 640, 640, 0, 0), {"max_crops": 4, "crop_size": 0}, "crop_size"),
+    ((640, 480, 0, 8, 640, 640, 0, 0), {"surrogate_mode": 2}, "surrogate_mode"),
+    ((640, 480, 0, 8, 640, 640, 0, 0), {"surrogate_mode": 1}, "surrogate"),                 # no thumbnails
+    ((640, 480, 0, 8, 640, 640, 0, 0), {"surrogate_mode": 1, "flags": 3, "num_blocks": 4}, "surrogate"),
+    ((640, 480, 0, 8, 640, 640, 0, 0), {"surrogate_mode": 1, "flags": 3, "schedule": 1}, "surrogate"),
+    ((640, 480, 0, 8, 640, 640, 0, 0), {"surrogate_mode": 1, "flags": 3, "judge_every": 0}, "judge_every"),
+    ((640, 480, 0, 8, 640, 640, 0, 0), {"surrogate_mode": 1, "flags": 3, "fallback_tol": -1.0}, "fallback_tol"),
 ])
 def test_invalid_configs_are_rejected(L, cam, kw, needle):
     from paper_1910_03517_gb300 import rt
