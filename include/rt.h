@@ -127,10 +127,13 @@ typedef struct {
  *                      method); 1: the learned surrogate (rt_surrogate.h)
  *                      predicts them from the previous frame set's
  *                      thumbnails and the fit runs only as its judge and
- *                      fallback -- needs RT_FIT_GLOBAL, one block,
- *                      RT_FLAG_THUMBNAILS, the current schedule and a network
- *                      (rt_surrogate_train or rt_surrogate_load) before the
- *                      first submit;
+ *                      fallback; 2: the same from the thumbnails of the frame
+ *                      set before the previous one, so that the prediction
+ *                      runs beside the previous frame set's correction pass
+ *                      instead of after it.  Modes 1 and 2 need RT_FIT_GLOBAL,
+ *                      one block, RT_FLAG_THUMBNAILS, the current schedule and
+ *                      a network (rt_surrogate_train or rt_surrogate_load)
+ *                      before the first submit;
  *   judge_every        surrogate mode: the fit judges the prediction every
  *                      judge_every-th frame set of a sequence (>= 1; 8);
  *   fallback_tol       surrogate mode: a judged prediction whose largest

@@ -144,8 +144,8 @@ rt_status validate(const rt_array_params *p)
         if (p->attn_min_on < 1) return fail(nullptr, RT_ERR_INVALID, "attn_min_on must be >= 1");
         if (p->attn_max < 1 || p->attn_max > 4096) return fail(nullptr, RT_ERR_INVALID, "attn_max must be in 1..4096");
     }
-    if (p->surrogate_mode != 0 && p->surrogate_mode != 1)
-        return fail(nullptr, RT_ERR_INVALID, "surrogate_mode must be 0 or 1");
+    if (p->surrogate_mode < 0 || p->surrogate_mode > 2)
+        return fail(nullptr, RT_ERR_INVALID, "surrogate_mode must be 0, 1 or 2");
     if (p->surrogate_mode) {
         if (p->fit_mode != RT_FIT_GLOBAL || p->num_blocks != 1 || !(p->flags & RT_FLAG_THUMBNAILS) ||
             p->schedule != RT_SCHED_CURRENT)
@@ -165,10 +165,10 @@ void free_all(rt_handle *h)
 {
     auto F = [](void *p) { if (p) cudaFree(p); };
     for (int i = 0; i < 2; ++i) {
-        F(h->rgb[i]); F(h->frame_hist[i]); F(h->thumbs[i]);
+        F(h->rgb[i]); F(h->frame_hist[i]);
         F(h->luma[i]); F(h->crops[i]); F(h->crop_dev[i]); F(h->stage[i]);
     }
-    for (int i = 0; i < 3; ++i) { F(h->strip_hist[i]); F(h->strip_sum[i]); }
+    for (int i = 0; i < 3; ++i) { F(h->strip_hist[i]); F(h->strip_sum[i]); F(h->thumbs[i]); }
     for (int i = 0; i < kQRing; ++i) F(h->q16[i]);
     F(h->maps_new); F(h->E); F(h->q16_identity); F(h->ramp); F(h->items); F(h->group_start);
     F(h->group_members); F(h->left_nbr); F(h->right_nbr); F(h->cam_H); F(h->seams);
@@ -275,14 +275,18 @@ rt_status setup(rt_handle *h)
         // groups around a window's last pixel
         if ((s = dalloc(h, &h->rgb[i], off + 64)) != RT_OK) return s;
         if ((s = dalloc(h, &h->frame_hist[i], (size_t)K * 768)) != RT_OK) return s;
-        if ((p.flags & RT_FLAG_THUMBNAILS) &&
-            (s = dalloc(h, &h->thumbs[i], (size_t)K * 3 * RT_THUMB_H * RT_THUMB_W)) != RT_OK) return s;
         h->luma_cam_stride = (size_t)2 * h->Hmax * S;
         if ((s = dalloc(h, &h->luma[i], (size_t)K * h->luma_cam_stride)) != RT_OK) return s;
         if (p.max_crops > 0) {
             if ((s = dalloc(h, &h->crops[i], (size_t)p.max_crops * 3 * p.crop_size * p.crop_size)) != RT_OK) return s;
             if ((s = dalloc(h, &h->crop_dev[i], (size_t)p.max_crops)) != RT_OK) return s;
         }
+    }
+    // thumbnail sums: a ring of three (the surrogate predicting frame set t
+    // from t-2 reads slot (t-2) % 3 while pass B(t-1) fills slot (t-1) % 3)
+    for (int i = 0; i < 3 && (p.flags & RT_FLAG_THUMBNAILS); ++i) {
+        rt_status s;
+        if ((s = dalloc(h, &h->thumbs[i], (size_t)K * 3 * RT_THUMB_H * RT_THUMB_W)) != RT_OK) return s;
     }
     if (p.max_crops > 0) RT_CUDA(h, cudaMallocHost((void **)&h->crop_host, sizeof(rt_crop) * 2 * p.max_crops));
     h->n_maps = (size_t)K * 2 * B * map_vals(p.fit_mode);
@@ -547,10 +551,12 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     // (pass B(t-1) done first) and the device-side decision whether the fit runs
     const bool sur = p.surrogate_mode != 0;
     if (sur) {
-        const int evp = (int)((t + kEvRing - 1) % kEvRing);
-        const bool dep1 = h->capturing ? (t - 1 >= h->cap_t0) : (t >= 1 && h->launched[evp]);
-        if (!first && dep1) RT_CUDA(h, cudaStreamWaitEvent(h->s_stats, h->ev_done[evp], 0));
-        rt_status s = surrogate_predict_step(h, h->thumbs[par ^ 1], first);
+        // the prediction reads the thumbnails of frame set t - lag (lag 1 or 2)
+        const int lag = p.surrogate_mode;
+        const int evp = (int)((t + kEvRing - lag) % kEvRing);
+        const bool dep = h->capturing ? (t - lag >= h->cap_t0) : (t >= lag && h->launched[evp]);
+        if (!first && dep) RT_CUDA(h, cudaStreamWaitEvent(h->s_stats, h->ev_done[evp], 0));
+        rt_status s = surrogate_predict_step(h, h->thumbs[(int)((t + 3 - lag) % 3)], first);
         if (s != RT_OK) return s;
     }
     // statistics chain: pass A -> solve
@@ -610,7 +616,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     // frame set (or at allocation); this pass B clears the other parity at
     // its end (it may start before the previous one ends, see k_pass_b.cu)
     uint32_t *fh = (p.flags & RT_FLAG_FRAME_STATS) ? h->frame_hist[par] : nullptr;
-    uint32_t *th = (p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[par] : nullptr;
+    uint32_t *th = (p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[(int)(t % 3)] : nullptr;
     PassBArgs pb{};
     pb.q16 = q_apply; pb.frame_hist = fh; pb.thumbs = th;
     if (h->q16_rows[0]) {
@@ -621,7 +627,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
         g.B = h->Hmax;
     }
     if (fh) { pb.clear_a = h->frame_hist[par ^ 1]; pb.clear_a_n = (uint32_t)K * 768; }
-    if (th) { pb.clear_b = h->thumbs[par ^ 1]; pb.clear_b_n = (uint32_t)K * 3 * RT_THUMB_H * RT_THUMB_W; }
+    if (th) { pb.clear_b = h->thumbs[(int)((t + 1) % 3)]; pb.clear_b_n = (uint32_t)K * 3 * RT_THUMB_H * RT_THUMB_W; }
     if (h->seams && dep2) RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_seam[ev2], 0));
     if (prof) RT_CUDA(h, prof_record(h, pe.b0, h->s_main));
     // the thumbnail variant with frame statistics needs the shared memory of
@@ -914,7 +920,7 @@ rt_status rt_get_stats(rt_handle *h, rt_stats_view *out, int32_t timeout_ms)
     out->strip_sumsq = reinterpret_cast<const uint64_t *>(h->strip_sumsq[ss]);
     out->strip_joint = reinterpret_cast<const uint64_t *>(h->strip_joint[ss]);
     out->frame_hist = (h->p.flags & RT_FLAG_FRAME_STATS) ? h->frame_hist[par] : nullptr;
-    out->thumbs = (h->p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[par] : nullptr;
+    out->thumbs = (h->p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[ss] : nullptr;
     out->num_cameras = h->p.num_cameras;
     out->num_blocks = h->p.num_blocks;
     return RT_OK;
@@ -966,7 +972,7 @@ rt_status rt_get_thumb_features(rt_handle *h, void *x_bf16, int32_t timeout_ms)
     if (h->t == 0) return fail(h, RT_ERR_STATE, "no frame set submitted");
     rt_status s = wait_event(h, h->ev_done[last_ev(h)], timeout_ms);
     if (s != RT_OK) return s;
-    RT_CUDA(h, launch_thumb_features(h->geom, h->thumbs[(int)((h->t - 1) & 1)], x_bf16, h->s_d2h));
+    RT_CUDA(h, launch_thumb_features(h->geom, h->thumbs[(int)((h->t - 1) % 3)], x_bf16, h->s_d2h));
     RT_CUDA(h, cudaEventRecord(h->ev_tmp, h->s_d2h));
     return wait_event(h, h->ev_tmp, timeout_ms);
 }

@@ -51,7 +51,7 @@ struct rt_handle {
     std::vector<size_t> rgb_off;
     size_t rgb_bytes = 0;
     uint32_t *frame_hist[2] = {nullptr, nullptr};
-    uint32_t *thumbs[2] = {nullptr, nullptr};
+    uint32_t *thumbs[3] = {nullptr, nullptr, nullptr};   // ring of three: frame set t in slot t % 3
     uint32_t *strip_hist[3] = {nullptr, nullptr, nullptr};
     uint32_t *strip_n[3] = {nullptr, nullptr, nullptr};
     unsigned long long *strip_sum[3] = {nullptr, nullptr, nullptr}, *strip_sumsq[3] = {nullptr, nullptr, nullptr};

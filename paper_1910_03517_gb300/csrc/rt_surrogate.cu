@@ -83,7 +83,7 @@ struct SurrogateState {
     // surrogate mode
     SgDev *dev = nullptr;
     double *pred = nullptr;        // predicted gains, layout of the maps [K][2][1][3][2]
-    bool skip_pred = false;        // the next frame set has no prediction (after a state restore)
+    int skip_pred = 0;             // frame sets without a prediction (after a state restore)
 };
 
 }  // namespace host
@@ -163,7 +163,7 @@ __global__ void eval_err_kernel(const float *__restrict__ y, const float *__rest
 // network's outputs y for the previous frame set's thumbnails) and whether
 // the plain fit runs.  One CTA.
 __global__ void __launch_bounds__(128) sg_decide_kernel(SgDev *__restrict__ st, const float *__restrict__ y, int first,
-                                                        int no_pred, int judge_every, const SolveTopo topo,
+                                                        int no_pred, int lag, int judge_every, const SolveTopo topo,
                                                         int n_groups, double gmin, double gmax,
                                                         double *__restrict__ pred)
 {
@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(128) sg_decide_kernel(SgDev *__restrict__ st, 
         } else {
             st->count += 1;
         }
-        st->have_pred = !(first || no_pred);
+        // a prediction needs frame set t - lag inside the sequence
+        st->have_pred = !(first || no_pred) && st->count >= lag;
         const int need = !st->have_pred || st->fallback || (st->count % judge_every) == 0;
         st->motion_ok = !first && st->ran_a;
         st->need_plain = need;
@@ -447,23 +448,24 @@ rt_status surrogate_ready(rt_handle *h)
 
 const int32_t *surrogate_gate(rt_handle *h) { return &h->sg->dev->need_plain; }
 
-// Statistics stream, before pass A(t): predict from the thumbnails of t-1
-// (none for the first frame set of a sequence or the first after a state
-// restore, whose predecessor's thumbnails are not part of the state).
+// Statistics stream, before pass A(t): predict from the thumbnails of frame
+// set t - lag (lag = surrogate_mode: 1, or 2 so that the inference overlaps
+// pass B(t-1)); none for the first lag frame sets of a sequence or after a
+// state restore (thumbnails are not part of the state).
 rt_status surrogate_predict_step(rt_handle *h, const uint32_t *prev_thumbs, bool first)
 {
     SurrogateState &S = *h->sg;
     const int K = h->p.num_cameras;
-    const bool no_pred = S.skip_pred && !h->capturing;
+    const bool no_pred = S.skip_pred > 0 && !h->capturing;
     if (!first && !no_pred) {
         RT_CUDA(h, launch_thumb_features(h->geom, prev_thumbs, mlp_input(S.net), h->s_stats));
         RT_CUDA(h, mlp_forward_async(S.net, K, h->s_stats));
     }
     sg_decide_kernel<<<1, 128, 0, h->s_stats>>>(S.dev, mlp_output(S.net), first ? 1 : 0, no_pred ? 1 : 0,
-                                                h->p.judge_every, h->solve_topo, h->n_groups, h->p.gain_min,
-                                                h->p.gain_max, S.pred);
+                                                h->p.surrogate_mode, h->p.judge_every, h->solve_topo, h->n_groups,
+                                                h->p.gain_min, h->p.gain_max, S.pred);
     RT_CUDA(h, cudaGetLastError());
-    if (!h->capturing) S.skip_pred = false;
+    if (!h->capturing && S.skip_pred > 0) --S.skip_pred;
     return RT_OK;
 }
 
@@ -490,7 +492,7 @@ rt_status surrogate_state_load(rt_handle *h, const uint8_t *in)
     rt_status s = surrogate_ready(h);
     if (s != RT_OK) return s;
     RT_CUDA(h, cudaMemcpy(h->sg->dev, in, sizeof(SgDev), cudaMemcpyHostToDevice));
-    h->sg->skip_pred = true;
+    h->sg->skip_pred = h->p.surrogate_mode;     // their thumbnails are not part of the state
     return RT_OK;
 }
 

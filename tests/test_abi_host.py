@@ -81,7 +81,7 @@ def _config(L, cams, **kw):
     ((640, 480, 0, 8, 640, 640, 0, 0), {"fit_mode": 4}, "fit_mode"),
     ((640, 480, 0, 8, 640, 640, 0, 0), {"gain_max": 17.0}, "gain_max"),
     ((640, 480, 0, 8, 640, 640, 0, 0), {"max_crops": 4, "crop_size": 0}, "crop_size"),
-    ((640, 480, 0, 8, 640, 640, 0, 0), {"surrogate_mode": 2}, "surrogate_mode"),
+    ((640, 480, 0, 8, 640, 640, 0, 0), {"surrogate_mode": 3}, "surrogate_mode"),
     ((640, 480, 0, 8, 640, 640, 0, 0), {"surrogate_mode": 1}, "surrogate"),                 # no thumbnails
     ((640, 480, 0, 8, 640, 640, 0, 0), {"surrogate_mode": 1, "flags": 3, "num_blocks": 4}, "surrogate"),
     ((640, 480, 0, 8, 640, 640, 0, 0), {"surrogate_mode": 1, "flags": 3, "schedule": 1}, "surrogate"),

@@ -12,8 +12,9 @@
 - The fallback switches on and off with the judgement: with an unreachable
   tolerance the prediction is applied (the fit runs every judge_every-th
   frame set) and the smoothed maps follow the prediction the handle's network
-  makes from the previous frame set's thumbnails; tolerance 0 turns the
-  fallback on at the next judgement, a large one off again.
+  makes from the thumbnails of frame set t - 1 (mode 1) or t - 2 (mode 2);
+  tolerance 0 turns the fallback on at the next judgement, a large one off
+  again.
 """
 import os
 import tempfile
@@ -96,11 +97,12 @@ def _sequence(cams, frames, seed=41):
     return [synth.frame_set(wl, t, device="cuda") for t in range(frames)]
 
 
-def test_tolerance_zero_is_the_plain_pipeline(rt):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_tolerance_zero_is_the_plain_pipeline(rt, mode):
     cams = _cams(8, 256, 144)
     seq = _sequence(cams, 10)
     plain = _array(rt, cams)
-    sur = _array(rt, cams, surrogate_mode=1, judge_every=3, fallback_tol=0.0)
+    sur = _array(rt, cams, surrogate_mode=mode, judge_every=3, fallback_tol=0.0)
     sur.surrogate_train(8 * 64, 128, 1e-3, seed=7)
     for t, fs in enumerate(seq):
         plain.submit_frames(fs, t)
@@ -113,7 +115,8 @@ def test_tolerance_zero_is_the_plain_pipeline(rt):
             assert torch.equal(plain.get_corrected(k), sur.get_corrected(k)), (t, k)
     r = sur.surrogate_report()
     assert r["frame_sets"] == 10 and r["plain"] == 10 and r["predicted"] == 0
-    assert r["judged"] == 9 and r["judged_failed"] == 9 and r["fallback"] == 1
+    # every frame set from `mode` on has a prediction to judge (and fails)
+    assert r["judged"] == 10 - mode and r["judged_failed"] == 10 - mode and r["fallback"] == 1
     plain.close()
     sur.close()
 
@@ -160,12 +163,34 @@ def test_fallback_switches_on_and_off(rt):
     arr.close()
 
 
-def test_surrogate_mode_captured_ring_matches_single_submits(rt):
+def test_lag_two_predicts_from_two_frame_sets_back(rt):
+    """Mode 2: frame set t gets the prediction made from frame set t-2's
+    thumbnails (frame sets 0 and 1 the fit's gains)."""
+    cams = _cams(8, 256, 144)
+    seq = _sequence(cams, 9)
+    arr = _array(rt, cams, surrogate_mode=2, judge_every=4, fallback_tol=1e9)
+    arr.surrogate_train(8 * 64, 128, 1e-3, seed=13)
+    preds, E_prev = {}, None
+    for t, fs in enumerate(seq):
+        arr.submit_frames(fs, t)
+        E, _ = arr.get_gains()
+        preds[t] = arr.surrogate_predict()[0]           # from frame set t's thumbnails
+        if t in (3, 5, 6, 7):                           # predicted, not judged (judged: 2 and 4 and 8)
+            assert np.abs(E - _expected_step(E_prev, preds[t - 2])).max() <= 1e-12 * np.abs(E).max(), t
+        E_prev = E
+    r = arr.surrogate_report()
+    # 0, 1: plain (no prediction yet); 2: judged, passes; 4, 8: judged
+    assert (r["plain"], r["predicted"], r["judged"], r["judged_failed"]) == (2, 7, 3, 0), r
+    arr.close()
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_surrogate_mode_captured_ring_matches_single_submits(rt, mode):
     cams = _cams(8, 256, 144)
     seq = _sequence(cams, 12)
     outs = []
     for captured in (False, True):
-        arr = _array(rt, cams, surrogate_mode=1, judge_every=4, fallback_tol=1e9)
+        arr = _array(rt, cams, surrogate_mode=mode, judge_every=4, fallback_tol=1e9)
         arr.surrogate_train(8 * 64, 128, 1e-3, seed=11)
         arr.submit_frames(seq[0], 0)
         if captured:
