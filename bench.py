@@ -186,7 +186,7 @@ def measured_peak():
 
 def pass_b_source_sha():
     h = hashlib.sha256()
-    for f in ("k_pass_b.cu", "pixel.cuh", "rt_internal.cuh"):
+    for f in ("k_pass_b.cu", "pass_b.cuh", "pixel.cuh", "rt_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1910_03517_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

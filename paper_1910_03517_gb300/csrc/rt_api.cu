@@ -169,7 +169,8 @@ void free_all(rt_handle *h)
         F(h->luma[i]); F(h->crops[i]); F(h->crop_dev[i]); F(h->stage[i]);
     }
     for (int i = 0; i < 3; ++i) { F(h->strip_hist[i]); F(h->strip_sum[i]); F(h->thumbs[i]); }
-    for (int i = 0; i < kQRing; ++i) F(h->q16[i]);
+    for (int i = 0; i < kQRing; ++i) { F(h->q16[i]); F(h->coef[i]); }
+    F(h->coef_identity);
     F(h->maps_new); F(h->E); F(h->q16_identity); F(h->ramp); F(h->items); F(h->group_start);
     F(h->group_members); F(h->left_nbr); F(h->right_nbr); F(h->cam_H); F(h->seams);
     F(h->seam_cost[0]); F(h->seam_cost[1]); F(h->seam_rows);
@@ -239,6 +240,7 @@ rt_status setup(rt_handle *h)
     h->rgb_off.resize(K);
     size_t off = 0;
     uint32_t units = 0;
+    uint64_t tiles = 0;
     h->Hmax = 0;
     for (int k = 0; k < K; ++k) {
         const rt_camera_desc &c = h->cams[k];
@@ -250,11 +252,17 @@ rt_status setup(rt_handle *h)
         cg.nblk = ((p.flags & RT_FLAG_BLEND_BLOCKS) && B > 1) ? c.height : B;
         cg.unit_base = units;
         units += cg.upr * (uint32_t)(c.height / 2);
+        // table variant: tiles of 8 row pairs x 4 units
+        cg.ntr = (c.height / 2 + 7) / 8;
+        cg.ntc = (int)((cg.upr + 3) / 4);
+        cg.tile_base = (uint32_t)tiles;
+        tiles += (uint64_t)cg.ntr * cg.ntc;
         h->rgb_off[k] = off;
         off += align_up((size_t)cg.rgb_pitch * c.height, 256);
         h->Hmax = std::max(h->Hmax, c.height);
     }
     g.units_total = units;
+    g.tiles_total = (uint32_t)tiles;   // <= units (a tile holds up to 32 units)
     h->rgb_bytes = off;
     for (int i = 0; i < 3; ++i) {
         rt_status s;
@@ -306,8 +314,9 @@ rt_status setup(rt_handle *h)
         RT_CUDA(h, cudaMemcpy(h->q16_identity, id.data(), id.size() * 4, cudaMemcpyHostToDevice));
     }
     // Q16 ramp weight per column, for the seam maps; each camera's ramp
-    // starts on 16 bytes and 16 bytes of tail follow the last one (pass B
-    // reads the weights of 4 columns at a time, past a ragged row end)
+    // starts on 16 bytes and 64 bytes of tail follow the last one (pass B
+    // reads the weights of 4 columns at a time up to the end of a ragged
+    // row's last unit, at most 12 columns past the camera's padded ramp)
     {
         std::vector<int32_t> rmp;
         std::vector<size_t> roff(K);
@@ -318,10 +327,26 @@ rt_status setup(rt_handle *h)
             for (long long x = 0; x < W; ++x)
                 rmp.push_back((int32_t)(x < half ? ((half - x) * 65536) / half : ((x - half + 1) * 65536) / half));
         }
-        for (int i = 0; i < 4; ++i) rmp.push_back(0);
+        for (int i = 0; i < 16; ++i) rmp.push_back(0);
         if ((s = dalloc(h, &h->ramp, rmp.size())) != RT_OK) return s;
         RT_CUDA(h, cudaMemcpy(h->ramp, rmp.data(), rmp.size() * 4, cudaMemcpyHostToDevice));
         for (int k = 0; k < K; ++k) g.cam[k].ramp = h->ramp + roff[k];
+    }
+    // seam maps applied per block (no blending): tables of the column
+    // coefficients the table variant of pass B reads, one per Q16 slot and
+    // one of the identity
+    if (p.fit_mode != RT_FIT_GLOBAL && !((p.flags & RT_FLAG_BLEND_BLOCKS) && B > 1)) {
+        const int nv = map_vals(p.fit_mode);
+        size_t words = 0;
+        for (int k = 0; k < K; ++k) {
+            g.cam[k].coef_base = (uint32_t)words;
+            words += (size_t)g.cam[k].nblk * ((g.cam[k].upr + 31) / 32) * 128 * nv;
+            if (words >= ((size_t)1 << 32)) return fail(h, RT_ERR_INVALID, "seam coefficient table too large");
+        }
+        for (int i = 0; i < kQRing; ++i)
+            if ((s = dalloc(h, &h->coef[i], words)) != RT_OK) return s;
+        if ((s = dalloc(h, &h->coef_identity, words)) != RT_OK) return s;
+        RT_CUDA(h, launch_seam_coef(g, h->q16_identity, nv, h->coef_identity, 0));
     }
     // pass A work items
     if ((s = build_items(h)) != RT_OK) return s;
@@ -414,6 +439,7 @@ rt_status setup(rt_handle *h)
         if ((s = dalloc(h, &h->attn_cells, cells)) != RT_OK) return s;
     }
     RT_CUDA(h, pass_b_prepare(h->pb_threads, &h->pb_smem));
+    RT_CUDA(h, pass_b_table_prepare());
     h->pb_grid = h->sm_count * h->pb_ctas;
     RT_CUDA(h, cudaDeviceSynchronize());
     return RT_OK;
@@ -593,16 +619,19 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
         rt_status s = surrogate_select_step(h, h->q16[qs], first);
         if (s != RT_OK) return s;
     }
+    if (h->coef[0]) RT_CUDA(h, launch_seam_coef(g, h->q16[qs], map_vals(p.fit_mode), h->coef[qs], h->s_solve));
     if (prof_chain) RT_CUDA(h, prof_record(h, pe.s1, h->s_solve));
     RT_CUDA(h, cudaEventRecord(h->ev_solved[ev], h->s_solve));
 
     // main chain: clear frame histograms -> pass B -> crops
     const int32_t *q_apply = h->q16[qs];
+    const uint4 *coef_apply = h->coef[qs];
     if (p.schedule == RT_SCHED_CURRENT) {
         RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_solved[ev], 0));
     } else {
         if (first) {
             q_apply = h->q16_identity;
+            coef_apply = h->coef_identity;
         } else {
             // inside a capture the first frame set's predecessor ran before the
             // graph starts (rt_launch_sequence orders the graph after it)
@@ -610,6 +639,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
             if (!h->capturing || t - 1 >= h->cap_t0)
                 RT_CUDA(h, cudaStreamWaitEvent(h->s_main, h->ev_solved[evp], 0));
             q_apply = h->q16[(int)((t + kQRing - 1) % kQRing)];
+            coef_apply = h->coef[(int)((t + kQRing - 1) % kQRing)];
         }
     }
     // accumulators of this parity were cleared by pass B of the previous
@@ -618,7 +648,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     uint32_t *fh = (p.flags & RT_FLAG_FRAME_STATS) ? h->frame_hist[par] : nullptr;
     uint32_t *th = (p.flags & RT_FLAG_THUMBNAILS) ? h->thumbs[(int)(t % 3)] : nullptr;
     PassBArgs pb{};
-    pb.q16 = q_apply; pb.frame_hist = fh; pb.thumbs = th;
+    pb.q16 = q_apply; pb.coef = coef_apply; pb.frame_hist = fh; pb.thumbs = th;
     if (h->q16_rows[0]) {
         // one blended map per row: the table pass B reads has Hmax "blocks"
         RT_CUDA(h, launch_blend_rows(g, q_apply, p.num_blocks, h->Hmax, map_vals(p.fit_mode), h->q16_rows[par],
@@ -632,9 +662,15 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     if (prof) RT_CUDA(h, prof_record(h, pe.b0, h->s_main));
     // the thumbnail variant with frame statistics needs the shared memory of
     // one CTA per SM; the seam maps run their own number per SM
-    const int pb_grid = (fh && th) ? h->sm_count
-                        : p.fit_mode != RT_FIT_GLOBAL ? h->sm_count * RT_PASS_B_SEAM_CTAS_PER_SM : h->pb_grid;
-    RT_CUDA(h, launch_pass_b(g, pb, pb_grid, h->pb_threads, h->pb_smem, h->s_main));
+    if (coef_apply) {
+        // seam maps, one per block: the table variant, one CTA per SM
+        RT_CUDA(h, launch_pass_b_table(g, pb, h->sm_count, th ? h->pb_threads : RT_PASS_B_TABLE_RUN_THREADS,
+                                       h->s_main));
+    } else {
+        const int pb_grid = (fh && th) ? h->sm_count
+                            : p.fit_mode != RT_FIT_GLOBAL ? h->sm_count * RT_PASS_B_SEAM_CTAS_PER_SM : h->pb_grid;
+        RT_CUDA(h, launch_pass_b(g, pb, pb_grid, h->pb_threads, h->pb_smem, h->s_main));
+    }
     if (prof) RT_CUDA(h, prof_record(h, pe.b1, h->s_main));
     const bool from_props = n_crops == RT_CROPS_FROM_PROPOSALS;
     if (from_props) {
@@ -1456,9 +1492,16 @@ rt_status rt_autotune(rt_handle *h, int32_t n_sets, const void *const *y_planes,
     h->t = t_saved;
     if (s == RT_OK) s = rt_load_state(h, state.data(), len);
     if (s == RT_OK && t_saved > 0) {
-        const cudaError_t e = cudaMemcpy(h->q16[(int)((t_saved - 1) % kQRing)], q_saved.data(), h->n_maps * 4,
-                                         cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) s = cuda_fail(h, e, "cudaMemcpy");
+        const int slot = (int)((t_saved - 1) % kQRing);
+        cudaError_t e = cudaMemcpy(h->q16[slot], q_saved.data(), h->n_maps * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            s = cuda_fail(h, e, "cudaMemcpy");
+        } else if (h->coef[0]) {
+            // and that slot's column coefficients
+            e = launch_seam_coef(h->geom, h->q16[slot], map_vals(h->p.fit_mode), h->coef[slot], h->s_solve);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->s_solve);
+            if (e != cudaSuccess) s = cuda_fail(h, e, "launch_seam_coef");
+        }
     }
     if (s != RT_OK) return s;
     best.step_us = best_us;

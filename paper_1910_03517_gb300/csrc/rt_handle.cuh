@@ -61,6 +61,11 @@ struct rt_handle {
     double *maps_new = nullptr, *E = nullptr;
     int32_t *q16[kQRing] = {nullptr, nullptr, nullptr};
     int32_t *q16_identity = nullptr;
+    // seam maps applied per block: the column coefficients of each Q16 slot
+    // (and of the identity) for the table variant of pass B, written after
+    // each solve
+    uint4 *coef[kQRing] = {nullptr, nullptr, nullptr};
+    uint4 *coef_identity = nullptr;
     int32_t *ramp = nullptr;
     rt::StripItem *items = nullptr;
     int n_items = 0;

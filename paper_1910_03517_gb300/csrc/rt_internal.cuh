@@ -32,14 +32,24 @@ namespace rt {
 #define RT_PASS_B_RUN_THREADS 352
 #endif
 
-// The seam-map variants of pass B (per-column coefficients of both rows of a
-// unit in registers) run RT_PASS_B_SEAM_CTAS_PER_SM CTAs of at most
+// The seam-map variants of pass B over units (blended per-row maps, or seam
+// maps beside the thumbnails; per-column coefficients of both rows of a unit
+// in registers) run RT_PASS_B_SEAM_CTAS_PER_SM CTAs of at most
 // RT_PASS_B_SEAM_THREADS threads per SM.
 #ifndef RT_PASS_B_SEAM_THREADS
 #define RT_PASS_B_SEAM_THREADS 512
 #endif
 #ifndef RT_PASS_B_SEAM_CTAS_PER_SM
 #define RT_PASS_B_SEAM_CTAS_PER_SM 1
+#endif
+// The table variant of pass B (seam maps per block) runs one CTA per SM of
+// RT_PASS_B_TABLE_RUN_THREADS threads, compiled for RT_PASS_B_TABLE_THREADS
+// (80 registers a thread; with thumbnails 512 threads and 128 registers).
+#ifndef RT_PASS_B_TABLE_THREADS
+#define RT_PASS_B_TABLE_THREADS 768
+#endif
+#ifndef RT_PASS_B_TABLE_RUN_THREADS
+#define RT_PASS_B_TABLE_RUN_THREADS 640
 #endif
 
 constexpr int kUnitCols = 16;          // columns a thread converts per row
@@ -59,6 +69,11 @@ struct CamGeom {
                             // (B; H when the table holds one map per row)
     uint32_t upr;           // units per row pair = ceil(W / 16)
     uint32_t unit_base;     // first unit of this camera in the array's unit space
+    // table variant of pass B (seam maps per block): a warp takes a tile of
+    // 8 row pairs x 4 units; ntr x ntc tiles per camera
+    uint32_t tile_base;     // first tile of this camera in the array's tile space
+    int32_t ntr, ntc;       // tiles per column (ceil(H / 16)), per row (ceil(upr / 4))
+    uint32_t coef_base;     // first 16-byte word of this camera in a coefficient table
     const int32_t *ramp;    // Q16 ramp weight per column (seam maps)
 };
 
@@ -76,11 +91,13 @@ struct ArrayGeom {
     ConvConsts conv;
     int32_t K, B, fit_mode, matrix;
     uint32_t units_total;   // sum over cameras of (H/2) * upr
+    uint32_t tiles_total;   // table variant: sum over cameras of ntr * ntc
 };
 
 // Pass B: conversion + whole-frame statistics + Q16 application.
 struct PassBArgs {
     const int32_t *q16;       // [K][2][B][3][2]
+    const uint4 *coef;        // table variant: column coefficients of q16 (launch_seam_coef)
     uint32_t *frame_hist;     // [K][3][256] (nullptr: statistics off)
     uint32_t *thumbs;         // [K][3][36][64] (nullptr: off)
     // the next frame set's accumulators (the other parity), cleared here
@@ -215,6 +232,19 @@ cudaError_t launch_synth(const SynthArgs &a, cudaStream_t s);
 cudaError_t launch_pass_b(const ArrayGeom &g, const PassBArgs &a, int grid, int threads,
                           size_t smem, cudaStream_t s);
 cudaError_t pass_b_prepare(int threads, size_t *smem_bytes);
+// Column coefficients of the seam maps q16[K][2][B][nv] (nv = 6 or 12, B =
+// every camera's nblk) for the table variant of pass B.  A camera's units
+// are taken in chunks of 32 (nch = ceil(upr / 32) a row); for block j, unit
+// ux = 32 chunk + l, group of 4 columns g4 and value v, the 16-byte word at
+//   coef[cam.coef_base + ((j * nch + chunk) * 4 + g4) * nv * 32 + 32 v + l]
+// holds value v (A_c then cst_c of the ramp blend, as the computing variant
+// derives them) of columns 16 ux + 4 g4 + 0..3.  Words per camera:
+// nblk * nch * 128 * nv.
+cudaError_t launch_seam_coef(const ArrayGeom &g, const int32_t *q16, int nv, uint4 *coef, cudaStream_t s);
+// Table variant of pass B (seam maps applied per block, a.coef set): grid
+// CTAs of threads over the array's tiles.
+cudaError_t launch_pass_b_table(const ArrayGeom &g, const PassBArgs &a, int grid, int threads, cudaStream_t s);
+cudaError_t pass_b_table_prepare();
 cudaError_t launch_pass_a(const ArrayGeom &g, const PassAArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s);
 cudaError_t launch_crops(const ArrayGeom &g, const CropArgs &a, int threads, int max_grid, cudaStream_t s);

@@ -516,4 +516,7 @@ def test_thumbnails_and_features(rt, orc):
             synth.Camera(90, 40, fmt=synth.MONO16, bit_depth=12, group=1, y_pitch=192)]
     wl = synth.Workload("ragged thumbs", cams, frames=2, seed=21)
     run_sequence(rt, orc, wl, 2, thumbs=True, strip_width=16, min_valid=8)
+    # seam maps beside the thumbnails (with and without frame statistics)
+    run_sequence(rt, orc, wl, 2, thumbs=True, strip_width=16, min_valid=8, fit_mode=1, num_blocks=3)
+    run_sequence(rt, orc, wl, 2, thumbs=True, stats=False, strip_width=16, min_valid=8, fit_mode=3, num_blocks=2)
     run_sequence(rt, orc, synth.tower12(frames=1), 1, thumbs=True, stats=False)
