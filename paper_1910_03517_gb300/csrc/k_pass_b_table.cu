@@ -42,6 +42,29 @@ __device__ __forceinline__ const uint4 *table_unit(const uint4 *__restrict__ coe
     return coef + cg.coef_base + (size_t)(j * nch + (ux >> 5)) * (4 * NV * 32) + (ux & 31);
 }
 
+// Coefficient words stay in L1 (evict last); the output does not allocate
+// there, so that streaming it does not evict them.
+__device__ __forceinline__ uint4 ld_coef(const uint4 *p)
+{
+    uint4 v;
+    asm("ld.global.nc.L1::evict_last.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_v8_na(uint8_t *p, const uint32_t (&w)[8])
+{
+    asm volatile("st.global.L1::no_allocate.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :: "l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_v4_na(uint8_t *p, const uint4 &w)
+{
+    asm volatile("st.global.L1::no_allocate.v4.b32 [%0], {%1, %2, %3, %4};"
+                 :: "l"(p), "r"(w.x), "r"(w.y), "r"(w.z), "r"(w.w) : "memory");
+}
+
 // One full row of a unit (48 bytes at a), as store_unit stores each row.
 __device__ __forceinline__ void store_row(const uint32_t (&w)[12], uint8_t *a)
 {
@@ -50,8 +73,8 @@ __device__ __forceinline__ void store_row(const uint32_t (&w)[12], uint8_t *a)
 #pragma unroll
     for (int i = 0; i < 8; ++i) w8[i] = odd ? w[4 + i] : w[i];
     const uint4 w4 = odd ? make_uint4(w[0], w[1], w[2], w[3]) : make_uint4(w[8], w[9], w[10], w[11]);
-    st_v8(a + (odd ? 16 : 0), w8);
-    *reinterpret_cast<uint4 *>(a + (odd ? 0 : 32)) = w4;
+    st_v8_na(a + (odd ? 16 : 0), w8);
+    st_v4_na(a + (odd ? 0 : 32), w4);
 }
 
 // A row's 48 bytes: the full row through store_row, a ragged one (nvalid
@@ -75,12 +98,12 @@ __device__ __forceinline__ void table_apply(const uint4 *__restrict__ tg, const 
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         if constexpr (NV == 6) {
-            const uint4 A = __ldg(tg + 32 * c), C = __ldg(tg + 32 * (3 + c));
+            const uint4 A = ld_coef(tg + 32 * c), C = ld_coef(tg + 32 * (3 + c));
 #pragma unroll
             for (int q = 0; q < 4; ++q) t[3 * q + c] = word_q(A, q) * vbq[q][c] + word_q(C, q);
         } else {
-            const uint4 A0 = __ldg(tg + 32 * (3 * c)), A1 = __ldg(tg + 32 * (3 * c + 1));
-            const uint4 A2 = __ldg(tg + 32 * (3 * c + 2)), C = __ldg(tg + 32 * (9 + c));
+            const uint4 A0 = ld_coef(tg + 32 * (3 * c)), A1 = ld_coef(tg + 32 * (3 * c + 1));
+            const uint4 A2 = ld_coef(tg + 32 * (3 * c + 2)), C = ld_coef(tg + 32 * (9 + c));
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 t[3 * q + c] = word_q(A0, q) * vbq[q][0] + word_q(A1, q) * vbq[q][1] + word_q(A2, q) * vbq[q][2] +
