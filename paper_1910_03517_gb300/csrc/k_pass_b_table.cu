@@ -42,27 +42,14 @@ __device__ __forceinline__ const uint4 *table_unit(const uint4 *__restrict__ coe
     return coef + cg.coef_base + (size_t)(j * nch + (ux >> 5)) * (4 * NV * 32) + (ux & 31);
 }
 
-// Coefficient words stay in L1 (evict last); the output does not allocate
-// there, so that streaming it does not evict them.
+// Coefficient words stay in L1 (evict last); the output stores do not
+// allocate there (st_v8, st_v4), so that streaming it does not evict them.
 __device__ __forceinline__ uint4 ld_coef(const uint4 *p)
 {
     uint4 v;
     asm("ld.global.nc.L1::evict_last.v4.u32 {%0,%1,%2,%3}, [%4];"
         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
     return v;
-}
-
-__device__ __forceinline__ void st_v8_na(uint8_t *p, const uint32_t (&w)[8])
-{
-    asm volatile("st.global.L1::no_allocate.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
-                 :: "l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
-                 : "memory");
-}
-
-__device__ __forceinline__ void st_v4_na(uint8_t *p, const uint4 &w)
-{
-    asm volatile("st.global.L1::no_allocate.v4.b32 [%0], {%1, %2, %3, %4};"
-                 :: "l"(p), "r"(w.x), "r"(w.y), "r"(w.z), "r"(w.w) : "memory");
 }
 
 // One full row of a unit (48 bytes at a), as store_unit stores each row.
@@ -73,8 +60,8 @@ __device__ __forceinline__ void store_row(const uint32_t (&w)[12], uint8_t *a)
 #pragma unroll
     for (int i = 0; i < 8; ++i) w8[i] = odd ? w[4 + i] : w[i];
     const uint4 w4 = odd ? make_uint4(w[0], w[1], w[2], w[3]) : make_uint4(w[8], w[9], w[10], w[11]);
-    st_v8_na(a + (odd ? 16 : 0), w8);
-    st_v4_na(a + (odd ? 0 : 32), w4);
+    st_v8(a + (odd ? 16 : 0), w8);
+    st_v4(a + (odd ? 0 : 32), w4);
 }
 
 // A row's 48 bytes: the full row through store_row, a ragged one (nvalid

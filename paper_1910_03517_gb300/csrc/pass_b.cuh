@@ -304,12 +304,20 @@ __device__ __forceinline__ void convert4(uint32_t yword, const ConvConsts &k, co
     }
 }
 
-// 256-bit store (32-byte aligned p).
+// Output stores: 256-bit (32-byte aligned p) and 128-bit, not allocating
+// in L1 (the output is written once and never read back by the kernel;
+// streaming it through L1 cost 5 % of pass B's time).
 __device__ __forceinline__ void st_v8(uint8_t *p, const uint32_t (&w)[8])
 {
-    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+    asm volatile("st.global.L1::no_allocate.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
                  :: "l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
                  : "memory");
+}
+
+__device__ __forceinline__ void st_v4(uint8_t *p, const uint4 &w)
+{
+    asm volatile("st.global.L1::no_allocate.v4.b32 [%0], {%1, %2, %3, %4};"
+                 :: "l"(p), "r"(w.x), "r"(w.y), "r"(w.z), "r"(w.w) : "memory");
 }
 
 // A full unit's two 48-byte rows, each as one 32-byte and one 16-byte store
@@ -332,7 +340,7 @@ __device__ __forceinline__ void store_unit(const uint32_t (&ow)[2][12], bool ful
         const uint4 w4 = odd ? make_uint4(ow[r][0], ow[r][1], ow[r][2], ow[r][3])
                              : make_uint4(ow[r][8], ow[r][9], ow[r][10], ow[r][11]);
         st_v8(a + (odd ? 16 : 0), w8);
-        *reinterpret_cast<uint4 *>(a + (odd ? 0 : 32)) = w4;
+        st_v4(a + (odd ? 0 : 32), w4);
     }
 }
 
