@@ -664,12 +664,13 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     // one CTA per SM; the seam maps run their own number per SM
     if (coef_apply) {
         // seam maps, one per block: the table variant, one CTA per SM
-        RT_CUDA(h, launch_pass_b_table(g, pb, h->sm_count, th ? h->pb_threads : RT_PASS_B_TABLE_RUN_THREADS,
+        RT_CUDA(h, launch_pass_b_table(g, pb, h->sm_count, th ? h->pb_threads_wide : RT_PASS_B_TABLE_RUN_THREADS,
                                        h->s_main));
     } else {
         const int pb_grid = (fh && th) ? h->sm_count
                             : p.fit_mode != RT_FIT_GLOBAL ? h->sm_count * RT_PASS_B_SEAM_CTAS_PER_SM : h->pb_grid;
-        RT_CUDA(h, launch_pass_b(g, pb, pb_grid, h->pb_threads, h->pb_smem, h->s_main));
+        const int pb_threads = th || p.fit_mode != RT_FIT_GLOBAL ? h->pb_threads_wide : h->pb_threads;
+        RT_CUDA(h, launch_pass_b(g, pb, pb_grid, pb_threads, h->pb_smem, h->s_main));
     }
     if (prof) RT_CUDA(h, prof_record(h, pe.b1, h->s_main));
     const bool from_props = n_crops == RT_CROPS_FROM_PROPOSALS;
@@ -1231,6 +1232,7 @@ rt_status apply_shape(rt_handle *h, const rt_tuning &t)
     if ((s = rt_sync(h, -1)) != RT_OK) return s;
     drop_sequence(h);
     h->pb_threads = t.pass_b_threads;
+    h->pb_threads_wide = t.pass_b_threads;
     h->pb_ctas = t.pass_b_ctas_per_sm;
     h->pb_grid = h->sm_count * h->pb_ctas;
     h->pa_threads = t.pass_a_threads;

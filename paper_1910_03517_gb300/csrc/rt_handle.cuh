@@ -124,8 +124,11 @@ struct rt_handle {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_mark = nullptr;
     bool prof_branch[3] = {false, false, false};   // the capture in progress used s_prof[i]
     // launch shapes (rt_autotune / rt_set_tuning)
-    int pb_grid = 0, pb_threads = RT_PASS_B_RUN_THREADS, pb_ctas = RT_PASS_B_CTAS_PER_SM;
-    int pa_rows = rt::host::kStripRows, pa_threads = 128, crop_threads = 256, crop_grid = 64;
+    int pb_grid = 0, pb_threads = RT_PASS_B_RUN_THREADS, pb_ctas = RT_PASS_B_RUN_CTAS;
+    // threads of the 128-register pass B variants (thumbnails, seam maps
+    // computed per unit): the tuned pb_threads once a shape is set
+    int pb_threads_wide = RT_PASS_B_WIDE_RUN_THREADS;
+    int pa_rows = rt::host::kStripRows, pa_threads = 64, crop_threads = 256, crop_grid = 64;
     rt_tuning tuned{};
     size_t pb_smem = 0;
     std::string err;

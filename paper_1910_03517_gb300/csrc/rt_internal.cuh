@@ -11,25 +11,31 @@
 
 namespace rt {
 
-// Pass B runs as a persistent grid of RT_PASS_B_CTAS_PER_SM CTAs per SM,
-// compiled for RT_PASS_B_THREADS threads (64 registers a thread) and
-// launched with RT_PASS_B_RUN_THREADS; each CTA holds its own 96 KB of
-// histograms.  Two CTAs per SM beat one: their barriers and tails do not
-// stall each other, and the next pass B takes over an SM half at a time.
-// Launching 384 of the 512 threads leaves 16K registers per SM to the band
-// statistics and the solve of the next frame set, which then run beside
-// pass B instead of waiting for its CTAs to exit.
+// Pass B (per-camera gains) is compiled for RT_PASS_B_CTAS_PER_SM CTAs of
+// RT_PASS_B_THREADS threads per SM (64 registers a thread) and runs, by
+// default, as a persistent grid of RT_PASS_B_RUN_CTAS CTAs per SM of
+// RT_PASS_B_RUN_THREADS threads; each CTA holds its own 96 KB of histograms.
+// The launch shape is a tuning parameter (rt_autotune).  With the output
+// stores bypassing L1, one CTA of 512 threads per SM, next to 64-thread
+// band-statistics CTAs, ran tower12 at 952k Mpix/s against 891k for two CTAs
+// of 352 threads: the registers left per SM let the next frame set's
+// statistics chain run beside pass B instead of waiting for its CTAs.
 #ifndef RT_PASS_B_THREADS
 #define RT_PASS_B_THREADS 512
 #endif
 #ifndef RT_PASS_B_CTAS_PER_SM
 #define RT_PASS_B_CTAS_PER_SM 2
 #endif
-// Threads a pass B CTA is launched with (at most RT_PASS_B_THREADS, which
-// sets the register budget): fewer leave registers on each SM for the
-// statistics chain of the next frame set to run beside pass B.
 #ifndef RT_PASS_B_RUN_THREADS
-#define RT_PASS_B_RUN_THREADS 352
+#define RT_PASS_B_RUN_THREADS 512
+#endif
+#ifndef RT_PASS_B_RUN_CTAS
+#define RT_PASS_B_RUN_CTAS 1
+#endif
+// Default threads of the pass B variants compiled for 128 registers (one CTA
+// per SM): thumbnails, and the seam maps computed per unit.
+#ifndef RT_PASS_B_WIDE_RUN_THREADS
+#define RT_PASS_B_WIDE_RUN_THREADS 352
 #endif
 
 // The seam-map variants of pass B over units (blended per-row maps, or seam

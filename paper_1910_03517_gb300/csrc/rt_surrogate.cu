@@ -396,7 +396,7 @@ rt_status gen_sample(rt_handle *h, uint64_t seed, int64_t set, __nv_bfloat16 *x_
     pb.thumbs = S.gen_thumbs[S.gen_par];
     pb.clear_b = S.gen_thumbs[S.gen_par ^ 1];
     pb.clear_b_n = (uint32_t)K * kMlpIn;
-    RT_CUDA(h, launch_pass_b(g, pb, h->sm_count, h->pb_threads, h->pb_smem, st));
+    RT_CUDA(h, launch_pass_b(g, pb, h->sm_count, h->pb_threads_wide, h->pb_smem, st));
     RT_CUDA(h, launch_thumb_features(g, S.gen_thumbs[S.gen_par], x_out, st));
     S.gen_par ^= 1;
     labels_kernel<<<1, 96, 0, st>>>(S.gen_maps, K, t_out);
