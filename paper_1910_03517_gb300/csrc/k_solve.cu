@@ -326,7 +326,10 @@ const SolveTables &solve_tables()
 // the ratio of two exact integer sums and b follows without FMA contraction
 // -- the oracle's arithmetic, operation for operation.
 constexpr int kQuantiles = 32;
-constexpr int kQuantWarps = 4;
+// One map per CTA (2 KB of shared memory): beside the table variant of
+// pass B, which leaves ~35 KB of shared memory per SM, CTAs of four maps
+// (8 KB) found too few free slots and the solve took 64 us a frame set.
+constexpr int kQuantWarps = 1;
 
 __global__ void __launch_bounds__(32 * kQuantWarps) solve_quantile_kernel(const SolveArgs a)
 {

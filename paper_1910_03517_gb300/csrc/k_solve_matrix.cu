@@ -39,7 +39,7 @@ namespace rt {
 
 namespace {
 
-constexpr int kMatWarps = 4;       // problems per CTA, one per sub-partition
+constexpr int kMatWarps = 1;       // problems per CTA
 constexpr int kNewtonMax = 12;
 constexpr double kRidge = 0.25;
 
