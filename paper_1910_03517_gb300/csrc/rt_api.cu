@@ -1425,6 +1425,7 @@ rt_status rt_autotune(rt_handle *h, int32_t n_sets, const void *const *y_planes,
     std::vector<uint8_t> state(len);
     if ((s = rt_save_state(h, state.data(), &len)) != RT_OK) return s;
     const int64_t t_saved = h->t;
+    const bool last_first_saved = h->last_first;
     // the Q16 table of the last frame set (the lagged schedule applies it next)
     std::vector<int32_t> q_saved;
     if (t_saved > 0) {
@@ -1490,8 +1491,10 @@ rt_status rt_autotune(rt_handle *h, int32_t n_sets, const void *const *y_planes,
     }
     rt_status s2 = apply_shape(h, best);
     if (s == RT_OK) s = s2;
-    // back to the sequence as it was
+    // back to the sequence as it was (whether the last frame set started the
+    // sequence decides which table the lagged schedule reports as applied)
     h->t = t_saved;
+    h->last_first = last_first_saved;
     if (s == RT_OK) s = rt_load_state(h, state.data(), len);
     if (s == RT_OK && t_saved > 0) {
         const int slot = (int)((t_saved - 1) % kQRing);

@@ -42,12 +42,16 @@ def _same(a, b):
     assert np.array_equal(a[4], b[4])
 
 
-def test_autotune_keeps_state_and_caches(rt, tmp_path):
+@pytest.mark.parametrize("kw", [{}, {"fit_mode": 1, "num_blocks": 16, "schedule": 1}])
+def test_autotune_keeps_state_and_caches(rt, tmp_path, kw):
+    """Also the seam maps under the lagged schedule: the frame set after the
+    tuning applies the restored Q16 slot through its coefficient table, which
+    the tuning's own frame sets had overwritten."""
     wl, frames, crops = _setup()
     K = len(wl.cams)
     cache = str(tmp_path / "tuning.json")
-    a = rt.CameraArray(wl.cams, max_crops=5, crop_size=40)
-    b = rt.CameraArray(wl.cams, max_crops=5, crop_size=40)
+    a = rt.CameraArray(wl.cams, max_crops=5, crop_size=40, **kw)
+    b = rt.CameraArray(wl.cams, max_crops=5, crop_size=40, **kw)
     a.submit_frames(frames[0], 0, crops[0])
     b.submit_frames(frames[0], 0, crops[0])
     before = a.get_gains()
@@ -65,7 +69,7 @@ def test_autotune_keeps_state_and_caches(rt, tmp_path):
         b.submit_frames(frames[i], i, crops[i])
         _same(_outputs(a, K), _outputs(b, K))
     # a cache hit applies the same shape without timing
-    c = rt.CameraArray(wl.cams, max_crops=5, crop_size=40)
+    c = rt.CameraArray(wl.cams, max_crops=5, crop_size=40, **kw)
     t2 = c.autotune([frames[i] for i in ring], [crops[i] for i in ring], cache_path=cache)
     assert t2["from_cache"] == 1 and t2["candidates"] == 0
     for k in ("pass_b_threads", "pass_b_ctas_per_sm", "pass_a_rows", "pass_a_threads", "crop_threads", "crop_grid"):
