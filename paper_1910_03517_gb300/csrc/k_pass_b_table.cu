@@ -145,6 +145,68 @@ __device__ __forceinline__ void unit_nv12_table(const CamGeom &cg, int rp, int u
     }
 }
 
+// An NV12 unit of the affine maps (6 words a column), both rows per
+// 4-column group: the group's six words are loaded once and serve both rows
+// (reloaded for row 1 when the row pair straddles a block boundary), the
+// chroma terms are converted once, and the unit's 2 x 12 output words go out
+// through store_unit.
+template <bool STATS, bool FULL, bool THUMBS>
+__device__ __forceinline__ void unit_nv12_table6(const CamGeom &cg, int rp, int ux, const ConvConsts &k,
+                                                 const uint4 *__restrict__ coef, uint32_t hbase, uint32_t *th,
+                                                 const uint4 Y0, const uint4 Y1, const uint4 UV, uint32_t (&ow)[2][12])
+{
+    const int x0 = ux * kUnitCols, y0 = rp * 2;
+    const int nvalid = FULL ? kUnitCols : (cg.W - x0);
+    const uint32_t yw[2][4] = {{Y0.x, Y0.y, Y0.z, Y0.w}, {Y1.x, Y1.y, Y1.z, Y1.w}};
+    const uint32_t uvw[4] = {UV.x, UV.y, UV.z, UV.w};
+    const int j0 = block_of_row(y0, cg.H, cg.nblk), j1 = block_of_row(y0 + 1, cg.H, cg.nblk);
+    const uint4 *tb[2] = {table_unit<6>(coef, cg, j0, ux), table_unit<6>(coef, cg, j1, ux)};
+    uint32_t tv[THUMBS ? 2 : 1][THUMBS ? kUnitCols : 1][3];
+#pragma unroll
+    for (int g4 = 0; g4 < 4; ++g4) {
+        const F2 Uf = bytes_f2(uvw[g4], 0, 2), Vf = bytes_f2(uvw[g4], 1, 3);
+        const F2 czR = fma2(Vf, k.krv, k.c_r0);
+        const F2 czG = fma2(Uf, k.kgu, fma2(Vf, k.kgv, k.c_g0));
+        const F2 czB = fma2(Uf, k.kbu, k.c_b0);
+        uint4 cf[6];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (r == 0 || j1 != j0) {
+                const uint4 *tg = tb[r] + g4 * 6 * 32;
+#pragma unroll
+                for (int v = 0; v < 6; ++v) cf[v] = ld_coef(tg + 32 * v);
+            }
+            uint32_t vbq[4][3];
+            convert4(yw[r][g4], k, czR, czG, czB, vbq);
+            uint32_t t[12];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = 4 * g4 + q;
+                const bool live = FULL || i < nvalid;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vbq[q][c];
+                    if (STATS && live) hist_inc(hbase + vbq[q][c] * 128u, c);
+                    t[3 * q + c] = word_q(cf[c], q) * vbq[q][c] + word_q(cf[3 + c], q);
+                }
+            }
+            ow[r][3 * g4 + 0] = even_bytes(clamp_hi2s(t[0], t[1]), clamp_hi2s(t[2], t[3]));
+            ow[r][3 * g4 + 1] = even_bytes(clamp_hi2s(t[4], t[5]), clamp_hi2s(t[6], t[7]));
+            ow[r][3 * g4 + 2] = even_bytes(clamp_hi2s(t[8], t[9]), clamp_hi2s(t[10], t[11]));
+        }
+    }
+    if constexpr (THUMBS) {
+        thumb_row<FULL>(th, cg, y0, x0, nvalid, tv[0]);
+        thumb_row<FULL>(th, cg, y0 + 1, x0, nvalid, tv[1]);
+    }
+    if (!FULL) {
+        for (int r = 0; r < 2; ++r) {
+            uint8_t *dst = cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0;
+            for (int b = 0; b < 3 * nvalid; ++b) dst[b] = (uint8_t)(ow[r][b >> 2] >> (8 * (b & 3)));
+        }
+    }
+}
+
 // A mono unit, row by row: the three channels of a pixel share its value.
 template <int NV, bool STATS, bool FULL, bool THUMBS>
 __device__ __forceinline__ void unit_mono_table(const CamGeom &cg, int rp, int ux, const uint4 *__restrict__ coef,
@@ -191,10 +253,14 @@ __device__ __forceinline__ void unit_mono_table(const CamGeom &cg, int rp, int u
     }
 }
 
-template <bool THUMBS> constexpr int kTableThreads = THUMBS ? 512 : RT_PASS_B_TABLE_THREADS;
+// The affine maps' kernel holds a 4-column group's six words for both rows
+// (96 registers: compiled for 640 threads, launched with at most 512); the
+// 3 x 3 maps' kernel works row by row (80 registers).
+template <int NV, bool THUMBS>
+constexpr int kTableThreads = THUMBS ? 512 : (NV == 6 ? 640 : RT_PASS_B_TABLE_THREADS);
 
 template <int NV, bool STATS, bool THUMBS>
-__global__ void __launch_bounds__(kTableThreads<THUMBS>, 1) pass_b_table_kernel(const ArrayGeom g, const PassBArgs a)
+__global__ void __launch_bounds__(kTableThreads<NV, THUMBS>, 1) pass_b_table_kernel(const ArrayGeom g, const PassBArgs a)
 {
     extern __shared__ uint32_t sh[];
     uint32_t *th = sh + (STATS ? kHistWords : 0);   // [36][64][3] cell sums (THUMBS)
@@ -228,10 +294,20 @@ __global__ void __launch_bounds__(kTableThreads<THUMBS>, 1) pass_b_table_kernel(
                 const uint8_t *yp = cg.y + (size_t)(2 * rp) * cg.y_pitch + ux * kUnitCols;
                 const uint4 Y0 = ld_stream(yp), Y1 = ld_stream(yp + cg.y_pitch);
                 const uint4 UV = ld_stream(cg.uv + (size_t)rp * cg.uv_pitch + ux * kUnitCols);
-                if (ux < full_units)
+                if constexpr (NV == 6) {
+                    uint32_t ow[2][12];
+                    if (ux < full_units) {
+                        unit_nv12_table6<STATS, true, THUMBS>(cg, rp, ux, k, a.coef, hbase, th, Y0, Y1, UV, ow);
+                        store_unit(ow, true, cg.rgb + (size_t)(2 * rp) * cg.rgb_pitch + 3 * kUnitCols * ux,
+                                   cg.rgb_pitch);
+                    } else {
+                        unit_nv12_table6<STATS, false, THUMBS>(cg, rp, ux, k, a.coef, hbase, th, Y0, Y1, UV, ow);
+                    }
+                } else if (ux < full_units) {
                     unit_nv12_table<NV, STATS, true, THUMBS>(cg, rp, ux, k, a.coef, hbase, th, Y0, Y1, UV);
-                else
+                } else {
                     unit_nv12_table<NV, STATS, false, THUMBS>(cg, rp, ux, k, a.coef, hbase, th, Y0, Y1, UV);
+                }
             } else {
                 if (ux < full_units)
                     unit_mono_table<NV, STATS, true, THUMBS>(cg, rp, ux, a.coef, hbase, th);
@@ -277,7 +353,7 @@ __global__ void __launch_bounds__(kTableThreads<THUMBS>, 1) pass_b_table_kernel(
 template <int NV, bool STATS, bool THUMBS>
 cudaError_t launch_table(const ArrayGeom &g, const PassBArgs &a, int grid, int threads, cudaStream_t s)
 {
-    if (threads > kTableThreads<THUMBS>) threads = kTableThreads<THUMBS>;
+    if (threads > kTableThreads<NV, THUMBS>) threads = kTableThreads<NV, THUMBS>;
     const size_t smem = (size_t)((STATS ? kHistWords : 0) + (THUMBS ? kThumbWords : 0)) * 4;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);

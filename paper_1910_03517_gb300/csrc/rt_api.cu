@@ -664,8 +664,9 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     // one CTA per SM; the seam maps run their own number per SM
     if (coef_apply) {
         // seam maps, one per block: the table variant, one CTA per SM
-        RT_CUDA(h, launch_pass_b_table(g, pb, h->sm_count, th ? h->pb_threads_wide : RT_PASS_B_TABLE_RUN_THREADS,
-                                       h->s_main));
+        const int tthreads = th ? h->pb_threads_wide
+                             : p.fit_mode == RT_FIT_MATRIX ? RT_PASS_B_TABLE_RUN_THREADS : RT_PASS_B_TABLE6_RUN_THREADS;
+        RT_CUDA(h, launch_pass_b_table(g, pb, h->sm_count, tthreads, h->s_main));
     } else {
         const int pb_grid = (fh && th) ? h->sm_count
                             : p.fit_mode != RT_FIT_GLOBAL ? h->sm_count * RT_PASS_B_SEAM_CTAS_PER_SM : h->pb_grid;

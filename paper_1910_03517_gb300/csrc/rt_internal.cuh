@@ -57,6 +57,11 @@ namespace rt {
 #ifndef RT_PASS_B_TABLE_RUN_THREADS
 #define RT_PASS_B_TABLE_RUN_THREADS 640
 #endif
+// The affine maps' table variant holds a 4-column group's coefficients for
+// both rows of a unit (96 registers): 512 threads per SM.
+#ifndef RT_PASS_B_TABLE6_RUN_THREADS
+#define RT_PASS_B_TABLE6_RUN_THREADS 512
+#endif
 
 constexpr int kUnitCols = 16;          // columns a thread converts per row
 
