@@ -15,10 +15,11 @@
 // of one unit column read the same coefficient words, so a warp's load of a
 // word touches 4 consecutive 16-byte words (one L1 wavefront) where a warp
 // along one row pair would touch 32.  Each row pair of 4 units is 192
-// contiguous output bytes.  A unit's two rows are converted, corrected and
-// stored one after the other, so that one row's output words are live at a
-// time.  Histograms and thumbnails as in k_pass_b.cu: one CTA per SM, a
-// contiguous slice of the array's tiles, one segment per camera.
+// contiguous output bytes.  Per 4-column group of a unit the group's
+// coefficient words are loaded once for both rows (again for the second row
+// when the row pair straddles a block boundary).  Histograms and thumbnails
+// as in k_pass_b.cu: one CTA per SM, a contiguous slice of the array's
+// tiles, one segment per camera.
 #include <algorithm>
 
 #include "pass_b.cuh"
@@ -99,59 +100,12 @@ __device__ __forceinline__ void table_apply(const uint4 *__restrict__ tg, const 
     }
 }
 
-// An NV12 unit (row pair rp, unit ux), row by row.
+// An NV12 unit, both rows per 4-column group: the group's NV words are
+// loaded once and serve both rows (reloaded for row 1 when the row pair
+// straddles a block boundary), the chroma terms are converted once, and the
+// unit's 2 x 12 output words go out through store_unit.
 template <int NV, bool STATS, bool FULL, bool THUMBS>
-__device__ __forceinline__ void unit_nv12_table(const CamGeom &cg, int rp, int ux, const ConvConsts &k,
-                                                const uint4 *__restrict__ coef, uint32_t hbase, uint32_t *th,
-                                                const uint4 Y0, const uint4 Y1, const uint4 UV)
-{
-    const int x0 = ux * kUnitCols, y0 = rp * 2;
-    const int nvalid = FULL ? kUnitCols : (cg.W - x0);
-    const uint32_t uvw[4] = {UV.x, UV.y, UV.z, UV.w};
-#pragma unroll 1
-    for (int r = 0; r < 2; ++r) {
-        const uint4 Yr = r ? Y1 : Y0;
-        const uint32_t yw[4] = {Yr.x, Yr.y, Yr.z, Yr.w};
-        const uint4 *tb = table_unit<NV>(coef, cg, block_of_row(y0 + r, cg.H, cg.nblk), ux);
-        uint32_t ow[12];
-        uint32_t tv[THUMBS ? kUnitCols : 1][3];
-#pragma unroll
-        for (int g4 = 0; g4 < 4; ++g4) {
-            const F2 Uf = bytes_f2(uvw[g4], 0, 2), Vf = bytes_f2(uvw[g4], 1, 3);
-            const F2 czR = fma2(Vf, k.krv, k.c_r0);
-            const F2 czG = fma2(Uf, k.kgu, fma2(Vf, k.kgv, k.c_g0));
-            const F2 czB = fma2(Uf, k.kbu, k.c_b0);
-            uint32_t vbq[4][3];
-            convert4(yw[g4], k, czR, czG, czB, vbq);
-            const uint4 *tg = tb + g4 * NV * 32;
-            uint32_t t[12];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int i = 4 * g4 + q;
-                const bool live = FULL || i < nvalid;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (THUMBS) tv[THUMBS ? i : 0][c] = vbq[q][c];
-                    if (STATS && live) hist_inc(hbase + vbq[q][c] * 128u, c);
-                }
-            }
-            table_apply<NV>(tg, vbq, t);
-            ow[3 * g4 + 0] = even_bytes(clamp_hi2s(t[0], t[1]), clamp_hi2s(t[2], t[3]));
-            ow[3 * g4 + 1] = even_bytes(clamp_hi2s(t[4], t[5]), clamp_hi2s(t[6], t[7]));
-            ow[3 * g4 + 2] = even_bytes(clamp_hi2s(t[8], t[9]), clamp_hi2s(t[10], t[11]));
-        }
-        if constexpr (THUMBS) thumb_row<FULL>(th, cg, y0 + r, x0, nvalid, tv);
-        put_row<FULL>(ow, cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0, nvalid);
-    }
-}
-
-// An NV12 unit of the affine maps (6 words a column), both rows per
-// 4-column group: the group's six words are loaded once and serve both rows
-// (reloaded for row 1 when the row pair straddles a block boundary), the
-// chroma terms are converted once, and the unit's 2 x 12 output words go out
-// through store_unit.
-template <bool STATS, bool FULL, bool THUMBS>
-__device__ __forceinline__ void unit_nv12_table6(const CamGeom &cg, int rp, int ux, const ConvConsts &k,
+__device__ __forceinline__ void unit_nv12_table2(const CamGeom &cg, int rp, int ux, const ConvConsts &k,
                                                  const uint4 *__restrict__ coef, uint32_t hbase, uint32_t *th,
                                                  const uint4 Y0, const uint4 Y1, const uint4 UV, uint32_t (&ow)[2][12])
 {
@@ -160,7 +114,7 @@ __device__ __forceinline__ void unit_nv12_table6(const CamGeom &cg, int rp, int 
     const uint32_t yw[2][4] = {{Y0.x, Y0.y, Y0.z, Y0.w}, {Y1.x, Y1.y, Y1.z, Y1.w}};
     const uint32_t uvw[4] = {UV.x, UV.y, UV.z, UV.w};
     const int j0 = block_of_row(y0, cg.H, cg.nblk), j1 = block_of_row(y0 + 1, cg.H, cg.nblk);
-    const uint4 *tb[2] = {table_unit<6>(coef, cg, j0, ux), table_unit<6>(coef, cg, j1, ux)};
+    const uint4 *tb[2] = {table_unit<NV>(coef, cg, j0, ux), table_unit<NV>(coef, cg, j1, ux)};
     uint32_t tv[THUMBS ? 2 : 1][THUMBS ? kUnitCols : 1][3];
 #pragma unroll
     for (int g4 = 0; g4 < 4; ++g4) {
@@ -168,13 +122,13 @@ __device__ __forceinline__ void unit_nv12_table6(const CamGeom &cg, int rp, int 
         const F2 czR = fma2(Vf, k.krv, k.c_r0);
         const F2 czG = fma2(Uf, k.kgu, fma2(Vf, k.kgv, k.c_g0));
         const F2 czB = fma2(Uf, k.kbu, k.c_b0);
-        uint4 cf[6];
+        uint4 cf[NV];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             if (r == 0 || j1 != j0) {
-                const uint4 *tg = tb[r] + g4 * 6 * 32;
+                const uint4 *tg = tb[r] + g4 * NV * 32;
 #pragma unroll
-                for (int v = 0; v < 6; ++v) cf[v] = ld_coef(tg + 32 * v);
+                for (int v = 0; v < NV; ++v) cf[v] = ld_coef(tg + 32 * v);
             }
             uint32_t vbq[4][3];
             convert4(yw[r][g4], k, czR, czG, czB, vbq);
@@ -187,7 +141,11 @@ __device__ __forceinline__ void unit_nv12_table6(const CamGeom &cg, int rp, int 
                 for (int c = 0; c < 3; ++c) {
                     if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vbq[q][c];
                     if (STATS && live) hist_inc(hbase + vbq[q][c] * 128u, c);
-                    t[3 * q + c] = word_q(cf[c], q) * vbq[q][c] + word_q(cf[3 + c], q);
+                    if constexpr (NV == 6)
+                        t[3 * q + c] = word_q(cf[c], q) * vbq[q][c] + word_q(cf[3 + c], q);
+                    else
+                        t[3 * q + c] = word_q(cf[3 * c], q) * vbq[q][0] + word_q(cf[3 * c + 1], q) * vbq[q][1] +
+                                       word_q(cf[3 * c + 2], q) * vbq[q][2] + word_q(cf[9 + c], q);
                 }
             }
             ow[r][3 * g4 + 0] = even_bytes(clamp_hi2s(t[0], t[1]), clamp_hi2s(t[2], t[3]));
@@ -253,11 +211,11 @@ __device__ __forceinline__ void unit_mono_table(const CamGeom &cg, int rp, int u
     }
 }
 
-// The affine maps' kernel holds a 4-column group's six words for both rows
-// (96 registers: compiled for 640 threads, launched with at most 512); the
-// 3 x 3 maps' kernel works row by row (80 registers).
+// Both kernels hold a 4-column group's words for both rows of a unit: the
+// affine maps' 6 (96 registers: compiled for 640 threads) and the 3 x 3
+// maps' 12 (128 registers: compiled for 512).
 template <int NV, bool THUMBS>
-constexpr int kTableThreads = THUMBS ? 512 : (NV == 6 ? 640 : RT_PASS_B_TABLE_THREADS);
+constexpr int kTableThreads = THUMBS ? 512 : (NV == 6 ? 640 : 512);
 
 template <int NV, bool STATS, bool THUMBS>
 __global__ void __launch_bounds__(kTableThreads<NV, THUMBS>, 1) pass_b_table_kernel(const ArrayGeom g, const PassBArgs a)
@@ -294,19 +252,12 @@ __global__ void __launch_bounds__(kTableThreads<NV, THUMBS>, 1) pass_b_table_ker
                 const uint8_t *yp = cg.y + (size_t)(2 * rp) * cg.y_pitch + ux * kUnitCols;
                 const uint4 Y0 = ld_stream(yp), Y1 = ld_stream(yp + cg.y_pitch);
                 const uint4 UV = ld_stream(cg.uv + (size_t)rp * cg.uv_pitch + ux * kUnitCols);
-                if constexpr (NV == 6) {
-                    uint32_t ow[2][12];
-                    if (ux < full_units) {
-                        unit_nv12_table6<STATS, true, THUMBS>(cg, rp, ux, k, a.coef, hbase, th, Y0, Y1, UV, ow);
-                        store_unit(ow, true, cg.rgb + (size_t)(2 * rp) * cg.rgb_pitch + 3 * kUnitCols * ux,
-                                   cg.rgb_pitch);
-                    } else {
-                        unit_nv12_table6<STATS, false, THUMBS>(cg, rp, ux, k, a.coef, hbase, th, Y0, Y1, UV, ow);
-                    }
-                } else if (ux < full_units) {
-                    unit_nv12_table<NV, STATS, true, THUMBS>(cg, rp, ux, k, a.coef, hbase, th, Y0, Y1, UV);
+                uint32_t ow[2][12];
+                if (ux < full_units) {
+                    unit_nv12_table2<NV, STATS, true, THUMBS>(cg, rp, ux, k, a.coef, hbase, th, Y0, Y1, UV, ow);
+                    store_unit(ow, true, cg.rgb + (size_t)(2 * rp) * cg.rgb_pitch + 3 * kUnitCols * ux, cg.rgb_pitch);
                 } else {
-                    unit_nv12_table<NV, STATS, false, THUMBS>(cg, rp, ux, k, a.coef, hbase, th, Y0, Y1, UV);
+                    unit_nv12_table2<NV, STATS, false, THUMBS>(cg, rp, ux, k, a.coef, hbase, th, Y0, Y1, UV, ow);
                 }
             } else {
                 if (ux < full_units)

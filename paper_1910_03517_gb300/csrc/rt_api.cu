@@ -665,7 +665,7 @@ rt_status enqueue(rt_handle *h, const void *const *y, const void *const *uv, int
     if (coef_apply) {
         // seam maps, one per block: the table variant, one CTA per SM
         const int tthreads = th ? h->pb_threads_wide
-                             : p.fit_mode == RT_FIT_MATRIX ? RT_PASS_B_TABLE_RUN_THREADS : RT_PASS_B_TABLE6_RUN_THREADS;
+                             : p.fit_mode == RT_FIT_MATRIX ? RT_PASS_B_TABLE12_RUN_THREADS : RT_PASS_B_TABLE6_RUN_THREADS;
         RT_CUDA(h, launch_pass_b_table(g, pb, h->sm_count, tthreads, h->s_main));
     } else {
         const int pb_grid = (fh && th) ? h->sm_count

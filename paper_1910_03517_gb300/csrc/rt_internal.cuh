@@ -48,17 +48,14 @@ namespace rt {
 #ifndef RT_PASS_B_SEAM_CTAS_PER_SM
 #define RT_PASS_B_SEAM_CTAS_PER_SM 1
 #endif
-// The table variant of pass B (seam maps per block) runs one CTA per SM of
-// RT_PASS_B_TABLE_RUN_THREADS threads, compiled for RT_PASS_B_TABLE_THREADS
-// (80 registers a thread; with thumbnails 512 threads and 128 registers).
-#ifndef RT_PASS_B_TABLE_THREADS
-#define RT_PASS_B_TABLE_THREADS 768
+// The table variant of pass B (seam maps per block) runs one CTA per SM:
+// the affine maps' kernel (96 registers) with RT_PASS_B_TABLE6_RUN_THREADS
+// threads, the 3 x 3 maps' (128 registers) with RT_PASS_B_TABLE12_RUN_THREADS;
+// more threads speed pass B up but leave the next frame set's statistics
+// chain no registers beside it.
+#ifndef RT_PASS_B_TABLE12_RUN_THREADS
+#define RT_PASS_B_TABLE12_RUN_THREADS 384
 #endif
-#ifndef RT_PASS_B_TABLE_RUN_THREADS
-#define RT_PASS_B_TABLE_RUN_THREADS 640
-#endif
-// The affine maps' table variant holds a 4-column group's coefficients for
-// both rows of a unit (96 registers): 512 threads per SM.
 #ifndef RT_PASS_B_TABLE6_RUN_THREADS
 #define RT_PASS_B_TABLE6_RUN_THREADS 512
 #endif
