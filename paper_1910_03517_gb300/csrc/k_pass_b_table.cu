@@ -187,7 +187,6 @@ __device__ __forceinline__ void unit_mono_table(const CamGeom &cg, int rp, int u
         for (int g4 = 0; g4 < 4; ++g4) {
             const uint4 *tg = tb + g4 * NV * 32;
             uint32_t t[12];
-#pragma unroll
             uint32_t vbq[4][3];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
