@@ -344,58 +344,55 @@ cudaError_t prepare_nv()
                                 kThumbWords * 4);
 }
 
-// The coefficient table: one thread per (camera, block j, chunk of 32 units,
-// 4-column group g4, unit) writes the NV words of columns 16 ux + 4 g4 +
-// 0..3 with col_coef (columns past the row end and units past the last one
-// of a chunk: weight 0).  Consecutive threads write consecutive words.
+// The coefficient table: one thread per (block j, chunk of 32 units,
+// 4-column group g4, unit) of camera blockIdx.y writes the NV words of
+// columns 16 ux + 4 g4 + 0..3 with col_coef (columns past the row end and
+// units past the last one of a chunk: weight 0).  Consecutive threads write
+// consecutive words.
 template <int NV>
 __global__ void __launch_bounds__(256) seam_coef_kernel(const ArrayGeom g, const int32_t *__restrict__ q16,
-                                                        uint4 *__restrict__ coef, uint32_t total)
+                                                        uint4 *__restrict__ coef)
 {
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-        int cam = 0;
-        while (cam + 1 < g.K && g.cam[cam + 1].coef_base / NV <= e) ++cam;
-        const CamGeom &cg = g.cam[cam];
-        const uint32_t local = e - cg.coef_base / NV;       // ((j nch + chunk) 4 + g4) 32 + l
-        const int l = (int)(local & 31u), g4 = (int)((local >> 5) & 3u);
-        const uint32_t jc = local >> 7;                      // j nch + chunk
-        const uint32_t nch = (cg.upr + 31) >> 5;
-        const int j = (int)(jc / nch), ux = (int)(jc % nch) * 32 + l;
-        const int half = cg.W >> 1;
-        uint32_t w[NV][4];
-        int m[NV];
-        int mside = -1;
+    const int cam = blockIdx.y;
+    const CamGeom &cg = g.cam[cam];
+    const uint32_t nch = (cg.upr + 31) >> 5;
+    const uint32_t local = blockIdx.x * blockDim.x + threadIdx.x;   // ((j nch + chunk) 4 + g4) 32 + l
+    if (local >= (uint32_t)cg.nblk * nch * 128u) return;
+    const int l = (int)(local & 31u), g4 = (int)((local >> 5) & 3u);
+    const uint32_t jc = local >> 7;                                  // j nch + chunk
+    const int j = (int)(jc / nch), ux = (int)(jc % nch) * 32 + l;
+    const int half = cg.W >> 1, xg = ux * kUnitCols + 4 * g4;
+    // the ramp table covers the last unit of a row (64 bytes of tail)
+    const int4 w4 = ramp4(cg.ramp, min(xg, (int)cg.upr * kUnitCols - 4));
+    const int wq[4] = {w4.x, w4.y, w4.z, w4.w};
+    uint32_t w[NV][4];
+    int m[NV];
+    load_map(q16, cam, xg >= half ? 1 : 0, j, g.B, m);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int x = ux * kUnitCols + 4 * g4 + q;
-            const int side = x >= half ? 1 : 0;
-            if (side != mside) {
-                load_map(q16, cam, side, j, g.B, m);
-                mside = side;
-            }
-            const int wr = x < cg.W ? __ldg(cg.ramp + x) : 0;
-            ColCoef<NV> cc;
-            col_coef(m, wr << 14, cc);
+    for (int q = 0; q < 4; ++q) {
+        const int x = xg + q;
+        if (xg < half && x == half) load_map(q16, cam, 1, j, g.B, m);
+        ColCoef<NV> cc;
+        col_coef(m, (x < cg.W ? wq[q] : 0) << 14, cc);
 #pragma unroll
-            for (int v = 0; v < NV - 3; ++v) w[v][q] = cc.A[v];
+        for (int v = 0; v < NV - 3; ++v) w[v][q] = cc.A[v];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) w[NV - 3 + c][q] = cc.cst[c];
-        }
-        uint4 *dst = coef + cg.coef_base + (size_t)jc * (4 * NV * 32) + g4 * NV * 32 + l;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) dst[32 * v] = make_uint4(w[v][0], w[v][1], w[v][2], w[v][3]);
+        for (int c = 0; c < 3; ++c) w[NV - 3 + c][q] = cc.cst[c];
     }
+    uint4 *dst = coef + cg.coef_base + (size_t)jc * (4 * NV * 32) + g4 * NV * 32 + l;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst[32 * v] = make_uint4(w[v][0], w[v][1], w[v][2], w[v][3]);
 }
 
 }  // namespace
 
 cudaError_t launch_seam_coef(const ArrayGeom &g, const int32_t *q16, int nv, uint4 *coef, cudaStream_t s)
 {
-    const CamGeom &last = g.cam[g.K - 1];
-    const uint32_t total = last.coef_base / (uint32_t)nv + (uint32_t)last.nblk * ((last.upr + 31) >> 5) * 128u;
-    const int grid = (int)std::min<uint32_t>((total + 255) / 256, 4096u);
-    if (nv == 12) seam_coef_kernel<12><<<grid, 256, 0, s>>>(g, q16, coef, total);
-    else seam_coef_kernel<6><<<grid, 256, 0, s>>>(g, q16, coef, total);
+    uint32_t most = 0;   // threads of the largest camera
+    for (int k = 0; k < g.K; ++k) most = std::max(most, (uint32_t)g.cam[k].nblk * ((g.cam[k].upr + 31) >> 5) * 128u);
+    const dim3 grid((most + 255) / 256, g.K);
+    if (nv == 12) seam_coef_kernel<12><<<grid, 256, 0, s>>>(g, q16, coef);
+    else seam_coef_kernel<6><<<grid, 256, 0, s>>>(g, q16, coef);
     return cudaGetLastError();
 }
 
