@@ -334,7 +334,8 @@ rt_status rt_launch_sequence(rt_handle *h);
 typedef struct {
     int32_t pass_b_threads;      /* threads per pass B CTA, 64..512, a multiple of 32 */
     int32_t pass_b_ctas_per_sm;  /* 1 or 2 (the thumbnail variant always runs 1) */
-    int32_t pass_a_rows;         /* rows per band-statistics work item, 8..1024 */
+    int32_t pass_a_rows;         /* rows per band-statistics work item, 8..1024 (a block's rows are
+                                    split into round(rows / pass_a_rows) equal items, at least one) */
     int32_t pass_a_threads;      /* threads per band-statistics CTA: 64, 128 or 256 */
     int32_t crop_threads;        /* threads per crop CTA, 128 or 256 (crops over 2048 pixels a
                                     side; smaller ones run crop_size / 2 threads a CTA) */

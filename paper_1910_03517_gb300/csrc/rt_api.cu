@@ -40,8 +40,10 @@ using namespace rt::host;
 
 namespace {
 
-// Band-statistics work items: (camera, side, block) rows split into chunks
-// of h->pa_rows rows (the device table is rebuilt when the shape changes).
+// Band-statistics work items: (camera, side, block) rows split into
+// round(rows / h->pa_rows) (at least one) chunks of equal size, so that a
+// block a little taller than pa_rows is one item, not one and a sliver (the
+// device table is rebuilt when the shape changes).
 rt_status build_items(rt_handle *h)
 {
     const int K = h->p.num_cameras, B = h->p.num_blocks;
@@ -51,10 +53,12 @@ rt_status build_items(rt_handle *h)
             for (int j = 0; j < B; ++j) {
                 const int H = h->cams[k].height;
                 const int r0 = (int)(((long long)j * H) / B), r1 = (int)(((long long)(j + 1) * H) / B);
-                for (int r = r0; r < r1; r += h->pa_rows) {
+                const int rows = r1 - r0, n = std::max(1, (rows + h->pa_rows / 2) / h->pa_rows);
+                for (int i = 0; i < n; ++i) {
                     StripItem it;
                     it.cam = (int16_t)k; it.side = (int16_t)side; it.block = (int16_t)j; it.pad = 0;
-                    it.row0 = r; it.row1 = std::min(r1, r + h->pa_rows);
+                    it.row0 = r0 + (int)(((long long)i * rows) / n);
+                    it.row1 = r0 + (int)(((long long)(i + 1) * rows) / n);
                     items.push_back(it);
                 }
             }
