@@ -332,7 +332,9 @@ rt_status rt_launch_sequence(rt_handle *h);
  * statistics and the crops are cut into CTAs) and on how they share the SMs
  * when they overlap, so rt_autotune measures them on the array itself. */
 typedef struct {
-    int32_t pass_b_threads;      /* threads per pass B CTA, 64..512, a multiple of 32 */
+    int32_t pass_b_threads;      /* threads per pass B CTA, 64..512, a multiple of 32 (the seam
+                                    maps applied per block without thumbnails run a fixed shape:
+                                    one CTA per SM of 512 threads, 384 for RT_FIT_MATRIX) */
     int32_t pass_b_ctas_per_sm;  /* 1 or 2 (the thumbnail variant always runs 1) */
     int32_t pass_a_rows;         /* rows per band-statistics work item, 8..1024 (a block's rows are
                                     split into round(rows / pass_a_rows) equal items, at least one) */

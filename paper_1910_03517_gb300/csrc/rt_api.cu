@@ -1457,8 +1457,10 @@ rt_status rt_autotune(rt_handle *h, int32_t n_sets, const void *const *y_planes,
     };
     // the shape in use first
     s = consider(best);
-    // stage 1: pass B
-    if (s == RT_OK) {
+    // stage 1: pass B (not for the seam maps' table variant without
+    // thumbnails, which runs its own fixed shape)
+    const bool fixed_pass_b = h->coef[0] && !(h->p.flags & RT_FLAG_THUMBNAILS);
+    if (s == RT_OK && !fixed_pass_b) {
         const rt_tuning base = best;
         for (int ctas = 1; ctas <= 2 && s == RT_OK; ++ctas)
             for (int thr : {256, 320, 352, 384, 448, 512}) {
