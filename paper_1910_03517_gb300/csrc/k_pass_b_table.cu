@@ -10,16 +10,19 @@
 // for the affine maps, 12 for the 3 x 3 maps) and applies them with the
 // computing variant's arithmetic, so the outputs are the same bits.
 //
-// Work decomposition: a warp takes a tile of 8 row pairs x 4 units (16 rows
-// x 64 columns); lane l does unit (8 tr + l / 4, 4 tc + l % 4).  The 8 lanes
-// of one unit column read the same coefficient words, so a warp's load of a
-// word touches 4 consecutive 16-byte words (one L1 wavefront) where a warp
-// along one row pair would touch 32.  Each row pair of 4 units is 192
-// contiguous output bytes.  Per 4-column group of a unit the group's
-// coefficient words are loaded once for both rows (again for the second row
-// when the row pair straddles a block boundary).  Histograms and thumbnails
-// as in k_pass_b.cu: one CTA per SM, a contiguous slice of the array's
-// tiles, one segment per camera.
+// Work decomposition: a warp takes a tile of kTileRowPairs x kTileUnits = 4
+// row pairs x 8 units (8 rows x 128 columns); lane l does unit (4 tr + l / 8,
+// 8 tc + l % 8).  The 4 lanes of one unit column read the same coefficient
+// words, so a warp's load of a word touches 8 consecutive 16-byte words (128
+// bytes) where a warp along one row pair would touch 32; each input load
+// reads 128 contiguous bytes of 4 rows, and each row pair of 8 units is 384
+// contiguous output bytes.  (Measured on tower12, affine maps: 4 x 8 tiles
+// 40.2 us per pass B in the pipeline; 8 x 4 42.9, 2 x 16 41.0, 16 x 2 48.9,
+// one row pair 41.6.)  Per 4-column group of a unit the group's coefficient
+// words are loaded once for both rows (again for the second row when the
+// row pair straddles a block boundary).  Histograms and thumbnails as in
+// k_pass_b.cu: one CTA per SM, a contiguous slice of the array's tiles, one
+// segment per camera.
 #include <algorithm>
 
 #include "pass_b.cuh"
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(kTableThreads<NV, THUMBS>, 1) pass_b_table_ker
         for (uint32_t t = tb + (uint32_t)warp; t < se; t += (uint32_t)nwarps) {
             const int local = (int)(t - cg.tile_base);
             const int tr = local / cg.ntc, tc = local - tr * cg.ntc;
-            const int rp = tr * 8 + (lane >> 2), ux = tc * 4 + (lane & 3);
+            const int rp = tr * kTileRowPairs + lane / kTileUnits, ux = tc * kTileUnits + lane % kTileUnits;
             if (rp >= nrp || ux >= (int)cg.upr) continue;
             if (cg.fmt == RT_NV12) {
                 const uint8_t *yp = cg.y + (size_t)(2 * rp) * cg.y_pitch + ux * kUnitCols;

@@ -256,9 +256,9 @@ rt_status setup(rt_handle *h)
         cg.nblk = ((p.flags & RT_FLAG_BLEND_BLOCKS) && B > 1) ? c.height : B;
         cg.unit_base = units;
         units += cg.upr * (uint32_t)(c.height / 2);
-        // table variant: tiles of 8 row pairs x 4 units
-        cg.ntr = (c.height / 2 + 7) / 8;
-        cg.ntc = (int)((cg.upr + 3) / 4);
+        // table variant: tiles of kTileRowPairs x kTileUnits units
+        cg.ntr = (c.height / 2 + kTileRowPairs - 1) / kTileRowPairs;
+        cg.ntc = (int)((cg.upr + kTileUnits - 1) / kTileUnits);
         cg.tile_base = (uint32_t)tiles;
         tiles += (uint64_t)cg.ntr * cg.ntc;
         h->rgb_off[k] = off;

@@ -61,6 +61,9 @@ namespace rt {
 #endif
 
 constexpr int kUnitCols = 16;          // columns a thread converts per row
+// Tile of a warp in the table variant of pass B: 4 row pairs x 8 units
+// (8 rows x 128 columns); lane l takes row pair l / 8, unit l % 8.
+constexpr int kTileRowPairs = 4, kTileUnits = 8;
 
 // Values of one (camera, side, block) map: 3 channels x (a, b), or a 3 x 3
 // cross-channel matrix (row-major) and its offset vector.
@@ -78,9 +81,9 @@ struct CamGeom {
     uint32_t upr;           // units per row pair = ceil(W / 16)
     uint32_t unit_base;     // first unit of this camera in the array's unit space
     // table variant of pass B (seam maps per block): a warp takes a tile of
-    // 8 row pairs x 4 units; ntr x ntc tiles per camera
+    // kTileRowPairs x kTileUnits units; ntr x ntc tiles per camera
     uint32_t tile_base;     // first tile of this camera in the array's tile space
-    int32_t ntr, ntc;       // tiles per column (ceil(H / 16)), per row (ceil(upr / 4))
+    int32_t ntr, ntc;       // tiles per column (ceil(H / 2 / kTileRowPairs)), per row (ceil(upr / kTileUnits))
     uint32_t coef_base;     // first 16-byte word of this camera in a coefficient table
     const int32_t *ramp;    // Q16 ramp weight per column (seam maps)
 };
