@@ -68,16 +68,26 @@ __device__ __forceinline__ void store_row(const uint32_t (&w)[12], uint8_t *a)
     st_v4(a + (odd ? 0 : 32), w4);
 }
 
+// The first nb bytes of a row's 12 words, byte by byte (a ragged unit).
+// Every word is named by a compile-time index, so that the words stay in
+// registers: a loop indexing them at run time puts the unit's output words
+// in local memory, stored there for every unit.
+__device__ __forceinline__ void put_ragged(const uint32_t (&w)[12], uint8_t *dst, int nb)
+{
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (4 * i + k < nb) dst[4 * i + k] = (uint8_t)(w[i] >> (8 * k));
+}
+
 // A row's 48 bytes: the full row through store_row, a ragged one (nvalid
-// columns) byte by byte.
+// columns) through put_ragged.
 template <bool FULL>
 __device__ __forceinline__ void put_row(const uint32_t (&ow)[12], uint8_t *dst, int nvalid)
 {
-    if (FULL) {
-        store_row(ow, dst);
-    } else {
-        for (int b = 0; b < 3 * nvalid; ++b) dst[b] = (uint8_t)(ow[b >> 2] >> (8 * (b & 3)));
-    }
+    if (FULL) store_row(ow, dst);
+    else put_ragged(ow, dst, 3 * nvalid);
 }
 
 // t of the 4 columns' channel c (t[3 q + c]) of a 4-column group from the
@@ -161,10 +171,8 @@ __device__ __forceinline__ void unit_nv12_table2(const CamGeom &cg, int rp, int 
         thumb_row<FULL>(th, cg, y0 + 1, x0, nvalid, tv[1]);
     }
     if (!FULL) {
-        for (int r = 0; r < 2; ++r) {
-            uint8_t *dst = cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0;
-            for (int b = 0; b < 3 * nvalid; ++b) dst[b] = (uint8_t)(ow[r][b >> 2] >> (8 * (b & 3)));
-        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) put_ragged(ow[r], cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0, 3 * nvalid);
     }
 }
 
