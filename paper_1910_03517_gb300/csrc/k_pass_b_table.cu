@@ -16,9 +16,9 @@
 // words, so a warp's load of a word touches 8 consecutive 16-byte words (128
 // bytes) where a warp along one row pair would touch 32; each input load
 // reads 128 contiguous bytes of 4 rows, and each row pair of 8 units is 384
-// contiguous output bytes.  (Measured on tower12, affine maps: 4 x 8 tiles
-// 40.2 us per pass B in the pipeline; 8 x 4 42.9, 2 x 16 41.0, 16 x 2 48.9,
-// one row pair 41.6.)  Per 4-column group of a unit the group's coefficient
+// contiguous output bytes.  (Of the tile shapes measured on tower12 with the
+// affine maps, 4 x 8 ran fastest, then 2 x 16, one row pair of 32 units,
+// 8 x 4 and 16 x 2.)  Per 4-column group of a unit the group's coefficient
 // words are loaded once for both rows (again for the second row when the
 // row pair straddles a block boundary).  Histograms and thumbnails as in
 // k_pass_b.cu: one CTA per SM, a contiguous slice of the array's tiles, one
