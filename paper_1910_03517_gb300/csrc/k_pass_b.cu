@@ -26,7 +26,8 @@ namespace rt {
 
 namespace {
 
-template <int FIT, bool STATS, bool FULL, bool THUMBS>
+// TH: no thumbnails (0) or the camera's thumbnail width class (pass_b.cuh).
+template <int FIT, bool STATS, bool FULL, int TH>
 __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, int ux, const ConvConsts &k,
                                           const int32_t *__restrict__ q16, int B, uint32_t hbase, uint32_t *th,
                                           bool seg, uint32_t sa0, uint32_t sa1, uint32_t sa2,
@@ -56,7 +57,9 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
         jr[0] = block_of_row(y0, cg.H, cg.nblk);
         jr[1] = block_of_row(y0 + 1, cg.H, cg.nblk);
     }
-    uint32_t tv[THUMBS ? 2 : 1][THUMBS ? kUnitCols : 1][3];
+    constexpr bool THUMBS = TH != 0;
+    [[maybe_unused]] ThumbAcc<2> ta;
+    if constexpr (THUMBS) thumb_begin<TH>(ta, cg, y0, x0);
 
 #pragma unroll
     for (int g4 = 0; g4 < 4; ++g4) {                  // pixels 4 g4 .. 4 g4 + 3
@@ -81,8 +84,10 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
                     const uint32_t *vb = vbq[q];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vb[c];
                         const bool live = FULL || i < nvalid;
+                        if constexpr (THUMBS) {
+                            if (live) thumb_add<TH>(ta, th, cg, r, x0, i, c, vb[c]);
+                        }
                         if (STATS && live) hist_inc(hbase + vb[c] * 128u, c);
                         t[3 * q + c] = rg[r].aq[c] * vb[c] + rg[r].cq[c];   // 65536 out + low bits, unclamped
                     }
@@ -119,7 +124,9 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
                     const bool live = FULL || i < nvalid;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vbq[r][q][c];
+                        if constexpr (THUMBS) {
+                            if (live) thumb_add<TH>(ta, th, cg, r, x0, i, c, vbq[r][q][c]);
+                        }
                         if (STATS && live) hist_inc(hbase + vbq[r][q][c] * 128u, c);
                     }
                 }
@@ -158,20 +165,27 @@ __device__ __forceinline__ void unit_nv12(const CamGeom &cg, int cam, int rp, in
         }
     }
     if constexpr (THUMBS) {
-        thumb_row<FULL>(th, cg, y0, x0, nvalid, tv[0]);
-        thumb_row<FULL>(th, cg, y0 + 1, x0, nvalid, tv[1]);
+        thumb_end<TH>(ta, th, nvalid);
     }
     // a full unit's 48 bytes per row go out through store_unit; a ragged one
     // writes its bytes here
     if (!FULL) {
-        for (int r = 0; r < 2; ++r) {
-            uint8_t *dst = cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0;
-            for (int b = 0; b < 3 * nvalid; ++b) dst[b] = (uint8_t)(ow[r][b >> 2] >> (8 * (b & 3)));
+        if constexpr (FIT == RT_FIT_GLOBAL && STATS && TH == 0) {
+            // this instance keeps its words in registers either way, and the
+            // unrolled stores would cost it registers
+            for (int r = 0; r < 2; ++r) {
+                uint8_t *dst = cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0;
+                for (int b = 0; b < 3 * nvalid; ++b) dst[b] = (uint8_t)(ow[r][b >> 2] >> (8 * (b & 3)));
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+                put_ragged(ow[r], cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0, 3 * nvalid);
         }
     }
 }
 
-template <int FIT, bool STATS, bool FULL, bool THUMBS>
+template <int FIT, bool STATS, bool FULL, int TH>
 __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, int ux,
                                           const int32_t *__restrict__ q16, int B, uint32_t hbase, uint32_t *th,
                                           uint32_t (&ow)[2][12])
@@ -197,12 +211,16 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
         constexpr int NV = FIT == RT_FIT_MATRIX ? 12 : 6;
         int mm[NV];
         int mside = -1;
-        uint32_t tv[THUMBS ? kUnitCols : 1][3];
+        [[maybe_unused]] ThumbAcc<1> ta;
+        if constexpr (TH != 0) thumb_begin<TH>(ta, cg, y0 + r, x0);
 #pragma unroll
         for (int i = 0; i < kUnitCols; ++i) {
             if (!FULL && i >= nvalid) continue;
             const uint32_t vb = mono_bits((w[i >> 1] >> (16 * (i & 1))) & 0xFFFFu, cg.shift);
-            if (THUMBS) tv[THUMBS ? i : 0][0] = tv[THUMBS ? i : 0][1] = tv[THUMBS ? i : 0][2] = vb;
+            if constexpr (TH != 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) thumb_add<TH>(ta, th, cg, 0, x0, i, c, vb);
+            }
             if constexpr (FIT != RT_FIT_GLOBAL) {
                 const int side = x0 + i >= (cg.W >> 1) ? 1 : 0;
                 if (side != mside) {
@@ -231,16 +249,42 @@ __device__ __forceinline__ void unit_mono(const CamGeom &cg, int cam, int rp, in
                 }
             }
         }
-        if constexpr (THUMBS) thumb_row<FULL>(th, cg, y0 + r, x0, nvalid, tv);
+        if constexpr (TH != 0) thumb_end<TH>(ta, th, nvalid);
     }
     // a full unit's 48 bytes per row go out through store_unit; a ragged one
     // writes its bytes here
     if (!FULL) {
-        for (int r = 0; r < 2; ++r) {
-            uint8_t *dst = cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0;
-            for (int b = 0; b < 3 * nvalid; ++b) dst[b] = (uint8_t)(ow[r][b >> 2] >> (8 * (b & 3)));
+        if constexpr (FIT == RT_FIT_GLOBAL && STATS && TH == 0) {
+            // this instance keeps its words in registers either way, and the
+            // unrolled stores would cost it registers
+            for (int r = 0; r < 2; ++r) {
+                uint8_t *dst = cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0;
+                for (int b = 0; b < 3 * nvalid; ++b) dst[b] = (uint8_t)(ow[r][b >> 2] >> (8 * (b & 3)));
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+                put_ragged(ow[r], cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0, 3 * nvalid);
         }
     }
+}
+
+// A unit with the camera's thumbnail width class (wide: TH = kThumbWide,
+// else kThumbNarrow), or without thumbnails.
+template <int FIT, bool STATS, bool FULL, bool THUMBS, typename... A>
+__device__ __forceinline__ void unit_nv12_th(bool wide, A &&...args)
+{
+    if constexpr (!THUMBS) unit_nv12<FIT, STATS, FULL, 0>(args...);
+    else if (wide) unit_nv12<FIT, STATS, FULL, kThumbWide>(args...);
+    else unit_nv12<FIT, STATS, FULL, kThumbNarrow>(args...);
+}
+
+template <int FIT, bool STATS, bool FULL, bool THUMBS, typename... A>
+__device__ __forceinline__ void unit_mono_th(bool wide, A &&...args)
+{
+    if constexpr (!THUMBS) unit_mono<FIT, STATS, FULL, 0>(args...);
+    else if (wide) unit_mono<FIT, STATS, FULL, kThumbWide>(args...);
+    else unit_mono<FIT, STATS, FULL, kThumbNarrow>(args...);
 }
 
 // The thumbnail variants get the registers of one CTA per SM, the seam maps
@@ -279,6 +323,7 @@ pass_b_kernel(const ArrayGeom g, const PassBArgs a)
         }
         const int upr = (int)cg.upr;
         const int full_units = cg.W / kUnitCols;
+        const bool twide = THUMBS && thumb_wide(cg);
         // per-camera gains hoisted out of the unit loop when there is one block
         const bool seg = FIT == RT_FIT_GLOBAL && g.B == 1;
         uint32_t sa0 = 0, sa1 = 0, sa2 = 0;
@@ -304,13 +349,13 @@ pass_b_kernel(const ArrayGeom g, const PassBArgs a)
                     const uint4 Y0 = ld_stream(yp), Y1 = ld_stream(yp + cg.y_pitch);
                     const uint4 UV = ld_stream(cg.uv + (size_t)rp * cg.uv_pitch + ux * kUnitCols);
                     if (ux < full_units) {
-                        unit_nv12<FIT, STATS, true, THUMBS>(cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg, sa0, sa1,
-                                                            sa2, Y0, Y1, UV, ow);
+                        unit_nv12_th<FIT, STATS, true, THUMBS>(twide, cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg,
+                                                                 sa0, sa1, sa2, Y0, Y1, UV, ow);
                         full = true;
                         dst0 = cg.rgb + (size_t)(2 * rp) * cg.rgb_pitch + 3 * kUnitCols * ux;
                     } else {
-                        unit_nv12<FIT, STATS, false, THUMBS>(cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg, sa0, sa1,
-                                                             sa2, Y0, Y1, UV, ow);
+                        unit_nv12_th<FIT, STATS, false, THUMBS>(twide, cg, cam, rp, ux, k, a.q16, g.B, hbase, th, seg,
+                                                                 sa0, sa1, sa2, Y0, Y1, UV, ow);
                     }
                 }
                 store_unit(ow, full, dst0, cg.rgb_pitch);
@@ -327,11 +372,11 @@ pass_b_kernel(const ArrayGeom g, const PassBArgs a)
                 uint8_t *dst0 = nullptr;
                 if (base + lane < nloc) {
                     if (ux < full_units) {
-                        unit_mono<FIT, STATS, true, THUMBS>(cg, cam, rp, ux, a.q16, g.B, hbase, th, ow);
+                        unit_mono_th<FIT, STATS, true, THUMBS>(twide, cg, cam, rp, ux, a.q16, g.B, hbase, th, ow);
                         full = true;
                         dst0 = cg.rgb + (size_t)(2 * rp) * cg.rgb_pitch + 3 * kUnitCols * ux;
                     } else {
-                        unit_mono<FIT, STATS, false, THUMBS>(cg, cam, rp, ux, a.q16, g.B, hbase, th, ow);
+                        unit_mono_th<FIT, STATS, false, THUMBS>(twide, cg, cam, rp, ux, a.q16, g.B, hbase, th, ow);
                     }
                 }
                 store_unit(ow, full, dst0, cg.rgb_pitch);

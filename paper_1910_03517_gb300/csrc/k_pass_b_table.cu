@@ -68,19 +68,6 @@ __device__ __forceinline__ void store_row(const uint32_t (&w)[12], uint8_t *a)
     st_v4(a + (odd ? 0 : 32), w4);
 }
 
-// The first nb bytes of a row's 12 words, byte by byte (a ragged unit).
-// Every word is named by a compile-time index, so that the words stay in
-// registers: a loop indexing them at run time puts the unit's output words
-// in local memory, stored there for every unit.
-__device__ __forceinline__ void put_ragged(const uint32_t (&w)[12], uint8_t *dst, int nb)
-{
-#pragma unroll
-    for (int i = 0; i < 12; ++i)
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (4 * i + k < nb) dst[4 * i + k] = (uint8_t)(w[i] >> (8 * k));
-}
-
 // A row's 48 bytes: the full row through store_row, a ragged one (nvalid
 // columns) through put_ragged.
 template <bool FULL>
@@ -117,7 +104,8 @@ __device__ __forceinline__ void table_apply(const uint4 *__restrict__ tg, const 
 // loaded once and serve both rows (reloaded for row 1 when the row pair
 // straddles a block boundary), the chroma terms are converted once, and the
 // unit's 2 x 12 output words go out through store_unit.
-template <int NV, bool STATS, bool FULL, bool THUMBS>
+// TH: no thumbnails (0) or the camera's thumbnail width class (pass_b.cuh).
+template <int NV, bool STATS, bool FULL, int TH>
 __device__ __forceinline__ void unit_nv12_table2(const CamGeom &cg, int rp, int ux, const ConvConsts &k,
                                                  const uint4 *__restrict__ coef, uint32_t hbase, uint32_t *th,
                                                  const uint4 Y0, const uint4 Y1, const uint4 UV, uint32_t (&ow)[2][12])
@@ -128,7 +116,9 @@ __device__ __forceinline__ void unit_nv12_table2(const CamGeom &cg, int rp, int 
     const uint32_t uvw[4] = {UV.x, UV.y, UV.z, UV.w};
     const int j0 = block_of_row(y0, cg.H, cg.nblk), j1 = block_of_row(y0 + 1, cg.H, cg.nblk);
     const uint4 *tb[2] = {table_unit<NV>(coef, cg, j0, ux), table_unit<NV>(coef, cg, j1, ux)};
-    uint32_t tv[THUMBS ? 2 : 1][THUMBS ? kUnitCols : 1][3];
+    constexpr bool THUMBS = TH != 0;
+    [[maybe_unused]] ThumbAcc<2> ta;
+    if constexpr (THUMBS) thumb_begin<TH>(ta, cg, y0, x0);
 #pragma unroll
     for (int g4 = 0; g4 < 4; ++g4) {
         const F2 Uf = bytes_f2(uvw[g4], 0, 2), Vf = bytes_f2(uvw[g4], 1, 3);
@@ -152,7 +142,9 @@ __device__ __forceinline__ void unit_nv12_table2(const CamGeom &cg, int rp, int 
                 const bool live = FULL || i < nvalid;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    if (THUMBS) tv[THUMBS ? r : 0][THUMBS ? i : 0][c] = vbq[q][c];
+                    if constexpr (THUMBS) {
+                        if (live) thumb_add<TH>(ta, th, cg, r, x0, i, c, vbq[q][c]);
+                    }
                     if (STATS && live) hist_inc(hbase + vbq[q][c] * 128u, c);
                     if constexpr (NV == 6)
                         t[3 * q + c] = word_q(cf[c], q) * vbq[q][c] + word_q(cf[3 + c], q);
@@ -167,8 +159,7 @@ __device__ __forceinline__ void unit_nv12_table2(const CamGeom &cg, int rp, int 
         }
     }
     if constexpr (THUMBS) {
-        thumb_row<FULL>(th, cg, y0, x0, nvalid, tv[0]);
-        thumb_row<FULL>(th, cg, y0 + 1, x0, nvalid, tv[1]);
+        thumb_end<TH>(ta, th, nvalid);
     }
     if (!FULL) {
 #pragma unroll
@@ -177,7 +168,7 @@ __device__ __forceinline__ void unit_nv12_table2(const CamGeom &cg, int rp, int 
 }
 
 // A mono unit, row by row: the three channels of a pixel share its value.
-template <int NV, bool STATS, bool FULL, bool THUMBS>
+template <int NV, bool STATS, bool FULL, int TH>
 __device__ __forceinline__ void unit_mono_table(const CamGeom &cg, int rp, int ux, const uint4 *__restrict__ coef,
                                                 uint32_t hbase, uint32_t *th)
 {
@@ -193,7 +184,8 @@ __device__ __forceinline__ void unit_mono_table(const CamGeom &cg, int rp, int u
         const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
         const uint4 *tb = table_unit<NV>(coef, cg, block_of_row(y0 + r, cg.H, cg.nblk), ux);
         uint32_t ow[12];
-        uint32_t tv[THUMBS ? kUnitCols : 1][3];
+        [[maybe_unused]] ThumbAcc<1> ta;
+        if constexpr (TH != 0) thumb_begin<TH>(ta, cg, y0 + r, x0);
 #pragma unroll
         for (int g4 = 0; g4 < 4; ++g4) {
             const uint4 *tg = tb + g4 * NV * 32;
@@ -207,7 +199,9 @@ __device__ __forceinline__ void unit_mono_table(const CamGeom &cg, int rp, int u
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     vbq[q][c] = v;
-                    if (THUMBS) tv[THUMBS ? i : 0][c] = v;
+                    if constexpr (TH != 0) {
+                        if (live) thumb_add<TH>(ta, th, cg, 0, x0, i, c, v);
+                    }
                     if (STATS && live) hist_inc(hbase + v * 128u, c);
                 }
             }
@@ -216,9 +210,27 @@ __device__ __forceinline__ void unit_mono_table(const CamGeom &cg, int rp, int u
             ow[3 * g4 + 1] = even_bytes(clamp_hi2s(t[4], t[5]), clamp_hi2s(t[6], t[7]));
             ow[3 * g4 + 2] = even_bytes(clamp_hi2s(t[8], t[9]), clamp_hi2s(t[10], t[11]));
         }
-        if constexpr (THUMBS) thumb_row<FULL>(th, cg, y0 + r, x0, nvalid, tv);
+        if constexpr (TH != 0) thumb_end<TH>(ta, th, nvalid);
         put_row<FULL>(ow, cg.rgb + (size_t)(y0 + r) * cg.rgb_pitch + 3 * x0, nvalid);
     }
+}
+
+// A unit with the camera's thumbnail width class (wide: TH = kThumbWide,
+// else kThumbNarrow), or without thumbnails.
+template <int NV, bool STATS, bool FULL, bool THUMBS, typename... A>
+__device__ __forceinline__ void unit_nv12_table_th(bool wide, A &&...args)
+{
+    if constexpr (!THUMBS) unit_nv12_table2<NV, STATS, FULL, 0>(args...);
+    else if (wide) unit_nv12_table2<NV, STATS, FULL, kThumbWide>(args...);
+    else unit_nv12_table2<NV, STATS, FULL, kThumbNarrow>(args...);
+}
+
+template <int NV, bool STATS, bool FULL, bool THUMBS, typename... A>
+__device__ __forceinline__ void unit_mono_table_th(bool wide, A &&...args)
+{
+    if constexpr (!THUMBS) unit_mono_table<NV, STATS, FULL, 0>(args...);
+    else if (wide) unit_mono_table<NV, STATS, FULL, kThumbWide>(args...);
+    else unit_mono_table<NV, STATS, FULL, kThumbNarrow>(args...);
 }
 
 // Both kernels hold a 4-column group's words for both rows of a unit: the
@@ -253,6 +265,7 @@ __global__ void __launch_bounds__(kTableThreads<NV, THUMBS>, 1) pass_b_table_ker
             __syncthreads();
         }
         const int nrp = cg.H >> 1, full_units = cg.W / kUnitCols;
+        const bool twide = THUMBS && thumb_wide(cg);
         for (uint32_t t = tb + (uint32_t)warp; t < se; t += (uint32_t)nwarps) {
             const int local = (int)(t - cg.tile_base);
             const int tr = local / cg.ntc, tc = local - tr * cg.ntc;
@@ -264,16 +277,18 @@ __global__ void __launch_bounds__(kTableThreads<NV, THUMBS>, 1) pass_b_table_ker
                 const uint4 UV = ld_stream(cg.uv + (size_t)rp * cg.uv_pitch + ux * kUnitCols);
                 uint32_t ow[2][12];
                 if (ux < full_units) {
-                    unit_nv12_table2<NV, STATS, true, THUMBS>(cg, rp, ux, k, a.coef, hbase, th, Y0, Y1, UV, ow);
+                    unit_nv12_table_th<NV, STATS, true, THUMBS>(twide, cg, rp, ux, k, a.coef, hbase, th, Y0, Y1,
+                                                                 UV, ow);
                     store_unit(ow, true, cg.rgb + (size_t)(2 * rp) * cg.rgb_pitch + 3 * kUnitCols * ux, cg.rgb_pitch);
                 } else {
-                    unit_nv12_table2<NV, STATS, false, THUMBS>(cg, rp, ux, k, a.coef, hbase, th, Y0, Y1, UV, ow);
+                    unit_nv12_table_th<NV, STATS, false, THUMBS>(twide, cg, rp, ux, k, a.coef, hbase, th, Y0, Y1,
+                                                                 UV, ow);
                 }
             } else {
                 if (ux < full_units)
-                    unit_mono_table<NV, STATS, true, THUMBS>(cg, rp, ux, a.coef, hbase, th);
+                    unit_mono_table_th<NV, STATS, true, THUMBS>(twide, cg, rp, ux, a.coef, hbase, th);
                 else
-                    unit_mono_table<NV, STATS, false, THUMBS>(cg, rp, ux, a.coef, hbase, th);
+                    unit_mono_table_th<NV, STATS, false, THUMBS>(twide, cg, rp, ux, a.coef, hbase, th);
             }
         }
         if (STATS || THUMBS) wait_prev_grid();   // the previous pass B cleared these accumulators

@@ -253,33 +253,74 @@ __device__ __forceinline__ uint32_t clamp24(uint32_t t)
     return (uint32_t)(v < 0 ? 0 : (v > 0xFFFFFF ? 0xFFFFFF : v));
 }
 
-// Thumbnail cell sums of one row's 16 converted pixels (vbits vb[i][c]):
-// cell (i, j) covers columns [floor(i W/64), floor((i+1) W/64)) and rows
-// [floor(j H/36), floor((j+1) H/36)); a unit inside one cell adds three
-// sums, a unit across cells adds per pixel.  th: shared [36][64][3] u32.
-template <bool FULL>
-__device__ __forceinline__ void thumb_row(uint32_t *th, const CamGeom &cg, int y, int x0, int nvalid,
-                                          const uint32_t (&vb)[kUnitCols][3])
+// Thumbnail cell sums of a unit's R rows.  Cell (i, j) covers columns
+// [floor(i W/64), floor((i+1) W/64)) and rows [floor(j H/36), floor((j+1)
+// H/36)); th is the shared [36][64][3] u32 array.  The width class TH of the
+// camera is fixed at compile time for the whole unit: on a camera at least
+// 16 x 64 columns wide (TH = 1) a 16-column unit spans at most two cells --
+// its columns before floor((c0 + 1) W/64), the first column of cell c0 + 1,
+// lie in the cell c0 of its first column, the others in c0 + 1 -- so every
+// row keeps, in registers, one sum per channel over its valid columns and
+// one over those in c0, added to the cells at the end.  On a narrower camera
+// (TH = 2) each value goes to its cell's shared word as it is converted.
+// Sums of value bits wrap modulo 2^32; the n kMagicBits they carry are taken
+// off at the end.
+constexpr int kThumbWide = 1, kThumbNarrow = 2;
+
+template <int R>
+struct ThumbAcc {
+    int c0, split;              // cell of the first column; columns of the unit in c0
+    int off[R];                 // th offsets of the rows' cell rows
+    uint32_t all[R][3], left[R][3];
+};
+
+// The width class of a camera's thumbnail sums (TH above).
+__device__ __forceinline__ bool thumb_wide(const CamGeom &cg) { return cg.W >= kUnitCols * RT_THUMB_W; }
+
+template <int TH, int R>
+__device__ __forceinline__ void thumb_begin(ThumbAcc<R> &t, const CamGeom &cg, int y0, int x0)
 {
-    const int cy = block_of_row(y, cg.H, RT_THUMB_H);
-    const int xl = x0 + (FULL ? kUnitCols : nvalid) - 1;
-    const int c0 = (int)(((x0 + 1) * RT_THUMB_W - 1) / cg.W), c1 = (int)(((xl + 1) * RT_THUMB_W - 1) / cg.W);
-    uint32_t *row = th + cy * RT_THUMB_W * 3;
-    if (c0 == c1) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            uint32_t sum = 0;
+    for (int r = 0; r < R; ++r) t.off[r] = block_of_row(y0 + r, cg.H, RT_THUMB_H) * RT_THUMB_W * 3;
+    if constexpr (TH == kThumbWide) {
+        t.c0 = (int)(((x0 + 1) * RT_THUMB_W - 1) / cg.W);
+        t.split = (int)((t.c0 + 1) * cg.W / RT_THUMB_W) - x0;
 #pragma unroll
-            for (int i = 0; i < kUnitCols; ++i)
-                if (FULL || i < nvalid) sum += vb[i][c] - kMagicBits;
-            atomicAdd(row + c0 * 3 + c, sum);
-        }
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) t.all[r][c] = t.left[r][c] = 0u;
+    }
+}
+
+// Value bits vb of channel c of valid column x0 + i, row r of the unit.
+template <int TH, int R>
+__device__ __forceinline__ void thumb_add(ThumbAcc<R> &t, uint32_t *th, const CamGeom &cg, int r, int x0, int i,
+                                          int c, uint32_t vb)
+{
+    if constexpr (TH == kThumbWide) {
+        t.all[r][c] += vb;
+        if (i < t.split) t.left[r][c] += vb;
     } else {
-        for (int i = 0; i < (FULL ? kUnitCols : nvalid); ++i) {
-            const int cx = (int)(((x0 + i + 1) * RT_THUMB_W - 1) / cg.W);
+        const int cx = (int)(((x0 + i + 1) * RT_THUMB_W - 1) / cg.W);
+        atomicAdd(th + t.off[r] + cx * 3 + c, vb - kMagicBits);
+    }
+}
+
+// The rows' sums into their cells (nvalid valid columns).
+template <int TH, int R>
+__device__ __forceinline__ void thumb_end(const ThumbAcc<R> &t, uint32_t *th, int nvalid)
+{
+    if constexpr (TH == kThumbWide) {
+        const int nl = min(t.split, nvalid), nr = nvalid - nl;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) atomicAdd(row + cx * 3 + c, vb[i][c] - kMagicBits);
-        }
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (nl > 0) atomicAdd(th + t.off[r] + t.c0 * 3 + c, t.left[r][c] - (uint32_t)nl * kMagicBits);
+                if (nr > 0)
+                    atomicAdd(th + t.off[r] + (t.c0 + 1) * 3 + c,
+                              t.all[r][c] - t.left[r][c] - (uint32_t)nr * kMagicBits);
+            }
     }
 }
 
@@ -318,6 +359,19 @@ __device__ __forceinline__ void st_v4(uint8_t *p, const uint4 &w)
 {
     asm volatile("st.global.L1::no_allocate.v4.b32 [%0], {%1, %2, %3, %4};"
                  :: "l"(p), "r"(w.x), "r"(w.y), "r"(w.z), "r"(w.w) : "memory");
+}
+
+// The first nb bytes of a row's 12 output words, byte by byte (a ragged
+// unit).  Every word is named by a compile-time index, so that the words stay
+// in registers: a loop indexing them at run time puts the unit's output words
+// in local memory, stored there for every unit.
+__device__ __forceinline__ void put_ragged(const uint32_t (&w)[12], uint8_t *dst, int nb)
+{
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (4 * i + k < nb) dst[4 * i + k] = (uint8_t)(w[i] >> (8 * k));
 }
 
 // A full unit's two 48-byte rows, each as one 32-byte and one 16-byte store
