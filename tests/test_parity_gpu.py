@@ -520,3 +520,11 @@ def test_thumbnails_and_features(rt, orc):
     run_sequence(rt, orc, wl, 2, thumbs=True, strip_width=16, min_valid=8, fit_mode=1, num_blocks=3)
     run_sequence(rt, orc, wl, 2, thumbs=True, stats=False, strip_width=16, min_valid=8, fit_mode=3, num_blocks=2)
     run_sequence(rt, orc, synth.tower12(frames=1), 1, thumbs=True, stats=False)
+
+
+@pytest.mark.parametrize("kw", [{}, {"fit_mode": 1, "num_blocks": 16}])
+def test_thumbnails_wide_cameras(rt, orc, kw):
+    """Cameras at least 16 x 64 columns wide sum a unit's thumbnail values in
+    registers (two cells at most per unit): the per-camera gains with frame
+    statistics and the seam maps' table variant, at full size."""
+    run_sequence(rt, orc, synth.tower12(frames=1), 1, thumbs=True, **kw)
